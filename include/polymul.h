@@ -1,0 +1,213 @@
+/*
+ * polymul.h -- C ABI of the GB300 (sm_103a) library for exact univariate
+ * polynomial multiplication over Z/pZ through the truncated Fourier transform.
+ *
+ * The method (Meng, "Automatic Library Generation for Modular Polynomial
+ * Multiplication", Section 3, Eq. (14)): with z1 = da+1, z2 = db+1,
+ * n = z1+z2-1 and L = 2^l >= n,
+ *     g^ = TFT(L, z1, n) g,   h^ = TFT(L, z2, n) h,   u^_i = g^_i h^_i (i < n),
+ *     (L u_0, ..., L u_{n-1}) = ITFT(L, n, n) u^,
+ * and u = g h (Definition 2, Eq. (2)).  This library returns u (it multiplies
+ * by L^-1 mod p); itft_exec can return the paper's L*u instead.
+ *
+ * Conventions shared by every entry point:
+ *  - Coefficients are uint32 residues, canonical in [0, p), a_i at index i
+ *    (Definition 1's dense representation).  Degrees are int64 (length =
+ *    degree + 1).  Inputs outside [0, p) give undefined (but memory-safe)
+ *    results; outputs are always canonical.
+ *  - p must be an odd prime below 2^31 with 2^k | p-1; the transform length L
+ *    must divide p-1 and not exceed 2^POLY_MAX_LOG_L.  root is a primitive
+ *    root of p, or 0 for the built-in table (469762049 -> 3, 2013265921 -> 31).
+ *    The principal L-th root used is w = root^((p-1)/L).
+ *  - L is the smallest power of two >= n (the paper only requires n <= L).
+ *  - TFT outputs are in van der Hoeven's bit-reversed order:
+ *    out_i = g(w^{rev_l(i)}) for i < n.
+ *  - Pointers marked "device" are CUDA device (or managed) memory owned by the
+ *    caller; "host" pointers are ordinary or pinned host memory.  Buffers must
+ *    not alias unless stated.  Plans, twiddle tables and workspaces are owned
+ *    by the library and stay resident until their destroy call (tables: until
+ *    the process exits).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  *_async calls only enqueue work and return; results are valid
+ *    once the stream reaches that point.
+ *  - Every call returns POLY_OK (0) or a negative error code; nothing traps.
+ *    Device-side waits are bounded and report POLY_ETIMEOUT.
+ */
+#ifndef POLYMUL_H
+#define POLYMUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POLY_OK 0
+#define POLY_EINVAL_PRIME (-1) /* p even, >= 2^31, or root not usable */
+#define POLY_ETOO_LONG (-2)    /* L does not divide p-1, or L > 2^POLY_MAX_LOG_L */
+#define POLY_ENULL (-3)        /* a required pointer is NULL */
+#define POLY_ENOMEM (-4)       /* device or host allocation failed */
+#define POLY_ECUDA (-5)        /* a CUDA runtime call failed */
+#define POLY_ETIMEOUT (-6)     /* a bounded device or host wait expired */
+#define POLY_EINVAL (-7)       /* a size or argument is out of range */
+#define POLY_EBUSY (-8)        /* request larger than the server's memory budget */
+#define POLY_ENOTFOUND (-9)    /* unknown server ticket */
+
+#define POLY_MAX_LOG_L 24
+
+/* Human-readable text for a status code (static storage). */
+const char *polymul_strerror(int status);
+
+/* Library version string. */
+const char *polymul_version(void);
+
+/*
+ * c = a * b mod p (Section 3, Eq. (14)).
+ *   a: device, da+1 words; b: device, db+1 words; c: device, da+db+1 words.
+ * polymul_mod is synchronous on the legacy default stream.
+ * polymul_mod_async enqueues on `stream`; its workspace comes from the
+ * stream-ordered allocator and is released on the same stream.
+ */
+int polymul_mod(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
+int polymul_mod_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                      uint32_t *c, void *stream);
+
+/*
+ * The zero-padded comparator of Eq. (12): both operands zero-padded to Lp
+ * (a power of two >= da+db+1), full size-Lp modular DFTs (no pruning of zero
+ * inputs or of outputs), pointwise product, full inverse.  c as above.
+ */
+int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                             uint32_t *c, int64_t Lp, void *stream);
+
+/*
+ * Host-buffer form: a, b, c are host pointers (pinned memory gives the best
+ * copy rate).  Copies in, multiplies and copies out on an internal stream;
+ * synchronous.
+ */
+int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
+
+/* ---------------------------------------------------------------- TFT plans */
+typedef struct tft_plan tft_plan;
+
+/*
+ * Plan for TFT(L, z, n) / ITFT(L, n, n) with L = smallest power of two >= n
+ * (Section 3).  Requires 1 <= z <= n.  One plan owns both directions, so the
+ * inverse mirrors the forward decomposition.
+ */
+int tft_plan_create(uint32_t p, uint32_t root, int64_t z, int64_t n, tft_plan **out);
+
+/* Transform length L of a plan (0 for NULL). */
+int64_t tft_plan_length(const tft_plan *plan);
+
+/* out[0..n) = TFT(L, z, n) in[0..z).  in, out: device; must not alias. */
+int tft_exec(const tft_plan *plan, const uint32_t *in, uint32_t *out, void *stream);
+
+/*
+ * out[0..n) = ITFT(L, n, n) in[0..n): the g of degree < n with
+ * TFT(L, g, n) = in.  scale = 1 returns g; scale = 0 returns L*g, the form
+ * Section 3 states.  in, out: device; must not alias.
+ */
+int itft_exec(const tft_plan *plan, const uint32_t *in, uint32_t *out, int scale, void *stream);
+
+void tft_plan_destroy(tft_plan *plan);
+
+/* ---------------------------------------------------------------- batched */
+typedef struct polymul_batch polymul_batch;
+
+/*
+ * Plan for `count` independent products mod p packed back to back:
+ * operand i of a occupies a[a_off[i] .. a_off[i+1]) (length = degree+1 >= 1),
+ * likewise b with b_off, and product i is written to c[c_off[i] ..
+ * c_off[i] + len_a + len_b - 1).  The offset arrays are HOST arrays of
+ * count+1 int64 entries; the plan copies them.  Schedules per size class come
+ * from the autotuned table (polymul_autotune) or the built-in defaults.
+ */
+int polymul_batch_create(uint32_t p, int64_t count, const int64_t *a_off, const int64_t *b_off,
+                         const int64_t *c_off, polymul_batch **out);
+
+/*
+ * Run the batch on device buffers a, b, c as one persistent kernel launch,
+ * replayed from a CUDA graph instantiated for this (a, b, c, stream) and
+ * cached in the plan.  Asynchronous on `stream`.
+ */
+int polymul_batch_exec(polymul_batch *batch, const uint32_t *a, const uint32_t *b, uint32_t *c, void *stream);
+
+/* Same work without the graph: the persistent kernel launched directly. */
+int polymul_batch_exec_nograph(polymul_batch *batch, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                               void *stream);
+
+/* Status of the last finished run (POLY_ETIMEOUT if a bounded wait expired).
+ * Synchronises with the batch's last launch. */
+int polymul_batch_status(polymul_batch *batch);
+
+void polymul_batch_destroy(polymul_batch *batch);
+
+/*
+ * One-shot convenience: create, exec and destroy (synchronous on `stream`).
+ * Offsets are host arrays as in polymul_batch_create.
+ */
+int polymul_mod_batched(uint32_t p, int64_t count, const uint32_t *a, const int64_t *a_off, const uint32_t *b,
+                        const int64_t *b_off, uint32_t *c, const int64_t *c_off, void *stream);
+
+/*
+ * The plain comparator for a batch: one polymul_mod_async call (its own
+ * launches) per product, in order, on `stream`.
+ */
+int polymul_mod_batched_plain(uint32_t p, int64_t count, const uint32_t *a, const int64_t *a_off,
+                              const uint32_t *b, const int64_t *b_off, uint32_t *c, const int64_t *c_off,
+                              void *stream);
+
+/* ---------------------------------------------------------------- autotuner */
+/*
+ * Time the candidate schedules (row block, column tile, threads) for every
+ * transform length 2^lo_log .. 2^hi_log on the current device and prime p,
+ * keep the fastest per length, and write the table as JSON to `json_path`
+ * (NULL: keep in memory only).  Subsequent plans use the table.
+ */
+int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path);
+
+/* Load a table written by polymul_autotune. */
+int polymul_load_schedules(const char *json_path);
+
+/* ---------------------------------------------------------------- serving */
+typedef struct polymul_server polymul_server;
+
+/*
+ * A continuous-batching server on the current device.  Requests are admitted
+ * while the bytes they hold (inputs, output and workspace) fit in
+ * mem_budget_bytes; the rest wait in arrival order.  Admitted requests are
+ * packed into persistent-kernel launches on `n_streams` streams, so work
+ * admitted while other work runs overlaps on the GPU.  Twiddle tables and
+ * plans for 469762049 and 2013265921 are made resident at creation.
+ */
+int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server **out);
+
+/*
+ * Submit c = a * b mod p.  a, b, c: device buffers owned by the caller, which
+ * must stay valid and untouched until the ticket is done.  Returns at once
+ * with a ticket.  POLY_EBUSY if the request alone exceeds the budget.
+ */
+int polymul_server_submit(polymul_server *srv, uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b,
+                          int64_t db, uint32_t *c, uint64_t *ticket);
+
+/* *done = 1 once the product is in c (and its status is returned), else 0. */
+int polymul_server_poll(polymul_server *srv, uint64_t ticket, int *done);
+
+/* Block until the ticket is done or timeout_ms passes (POLY_ETIMEOUT). */
+int polymul_server_wait(polymul_server *srv, uint64_t ticket, int64_t timeout_ms);
+
+/*
+ * Latency statistics of completed requests (submit -> GPU completion), in
+ * microseconds: out[0..5] = {count, p50, p90, p99, max, mean}.
+ */
+int polymul_server_stats(polymul_server *srv, double *out6);
+
+int polymul_server_destroy(polymul_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYMUL_H */

@@ -1,0 +1,136 @@
+// autotune.cu -- empirical schedule search (the counterpart of the paper's
+// dynamic-programming search that times candidate breakdowns, Section 4).
+//
+// For each transform length L = 2^l of the three-kernel path, every valid
+// (sigma, C) pair -- sigma sets where the tree is split between the column
+// and row stages (row length 2^sigma, radix-16 Stockham passes inside a row),
+// C the column-tile width -- is timed on a full-length product (n = L - 1)
+// with CUDA events; the fastest is kept and used by later plans.  The table
+// is written as JSON:
+//   {"device": "...", "p": P, "schedules": [{"l": 20, "sigma": 11, "C": 16, "us": 12.3}, ...]}
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "host.h"
+#include "polymul.h"
+
+using namespace pm;
+
+static float time_schedule(PrimeCtx *ctx, int l, Schedule sch, const u32 *a, const u32 *b, u32 *c, u32 *ws,
+                           cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    const int64_t L = (int64_t)1 << l, z = L / 2;
+    LargeDesc d;
+    if (prepare_large(ctx, a, z, b, z, c, l, true, sch, &d)) return -1.f;
+    d.wa = ws;
+    d.wb = ws + d.g.k * d.g.S;
+    std::vector<float> t;
+    for (int it = 0; it < 8; ++it) {
+        cudaEventRecord(e0, st);
+        if (launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st) != cudaSuccess) return -1.f;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it >= 2) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2] * 1000.f;
+}
+
+extern "C" {
+
+int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path) {
+    if (lo_log < SMALL_MAX_LOG_L + 1) lo_log = SMALL_MAX_LOG_L + 1;
+    if (hi_log > POLY_MAX_LOG_L || hi_log < lo_log) return POLY_EINVAL;
+    PrimeCtx *ctx = nullptr;
+    int rc = get_prime(p, 0, hi_log, &ctx, nullptr);
+    if (rc) return rc;
+    cudaStream_t st;
+    cudaEvent_t e0, e1;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return POLY_ECUDA;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int64_t Lmax = (int64_t)1 << hi_log;
+    u32 *buf = nullptr;
+    // a, b (L/2 each), c (L), workspace (2L)
+    if (cudaMalloc(&buf, (size_t)(Lmax / 2 * 2 + Lmax + 2 * Lmax) * 4) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return POLY_ENOMEM;
+    }
+    u32 *a = buf, *b = buf + Lmax / 2, *c = b + Lmax / 2, *ws = c + Lmax;
+    cudaMemsetAsync(a, 0x01, (size_t)Lmax * 4, st);
+    struct Row {
+        int l;
+        Schedule s;
+        float us;
+    };
+    std::vector<Row> rows;
+    for (int l = lo_log; l <= hi_log; ++l) {
+        Schedule best{0, 0};
+        float best_us = 1e30f;
+        for (int sigma = 9; sigma <= 13; ++sigma)
+            for (int C : {8, 16, 32}) {
+                Schedule s{sigma, C};
+                if (!schedule_valid(l, s)) continue;
+                const float us = time_schedule(ctx, l, s, a, b, c, ws, st, e0, e1);
+                if (us > 0 && us < best_us) {
+                    best_us = us;
+                    best = s;
+                }
+            }
+        if (best.sigma) {
+            set_schedule(l, best);
+            rows.push_back(Row{l, best, best_us});
+        }
+    }
+    cudaFree(buf);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (json_path) {
+        FILE *f = fopen(json_path, "w");
+        if (!f) return POLY_EINVAL;
+        cudaDeviceProp prop;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaGetDeviceProperties(&prop, dev);
+        fprintf(f, "{\"device\": \"%s\", \"p\": %u, \"schedules\": [\n", prop.name, p);
+        for (size_t i = 0; i < rows.size(); ++i)
+            fprintf(f, "  {\"l\": %d, \"sigma\": %d, \"C\": %d, \"us\": %.3f}%s\n", rows[i].l, rows[i].s.sigma,
+                    rows[i].s.C, rows[i].us, i + 1 < rows.size() ? "," : "");
+        fprintf(f, "]}\n");
+        fclose(f);
+    }
+    return POLY_OK;
+}
+
+int polymul_load_schedules(const char *json_path) {
+    if (!json_path) return POLY_ENULL;
+    FILE *f = fopen(json_path, "r");
+    if (!f) return POLY_EINVAL;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    fclose(f);
+    size_t pos = 0;
+    int loaded = 0;
+    while ((pos = text.find("{\"l\":", pos)) != std::string::npos) {
+        int l = 0, sigma = 0, C = 0;
+        if (sscanf(text.c_str() + pos, "{\"l\": %d, \"sigma\": %d, \"C\": %d", &l, &sigma, &C) == 3) {
+            Schedule s{sigma, C};
+            if (schedule_valid(l, s)) {
+                set_schedule(l, s);
+                ++loaded;
+            }
+        }
+        pos += 5;
+    }
+    return loaded > 0 ? POLY_OK : POLY_EINVAL;
+}
+
+}  // extern "C"

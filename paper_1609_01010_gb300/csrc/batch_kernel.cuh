@@ -1,0 +1,124 @@
+// batch_kernel.cuh -- the persistent batched kernel (see batch.cu for the
+// work-list protocol).
+#pragma once
+#include <map>
+#include <mutex>
+
+#include "batch.h"
+#include "bodies.cuh"
+#include "polymul.h"
+
+namespace pm {
+
+__device__ __forceinline__ bool wait_count(const int *ctr, int target, int *status, long long limit) {
+    long long it = 0;
+    while (*(volatile const int *)ctr < target) {
+        if (++it > limit) {
+            atomicExch(status, POLY_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    __threadfence();
+    return true;
+}
+
+template <class A, int C>
+__global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchParams P) {
+    __shared__ int s_item, s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= P.nitems) break;
+        const WorkItem w = P.items[it];
+        const BatchDesc bd = P.descs[w.prod];
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (w.kind == IT_ROW)
+                ok = wait_count(P.counters + 2 * w.prod, 2 * (int)(bd.g.S / C), P.status, P.spin_limit);
+            else if (w.kind == IT_COLI)
+                ok = wait_count(P.counters + 2 * w.prod + 1, (int)bd.g.k, P.status, P.spin_limit);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            const u32 *pa = (const u32 *)((uintptr_t)P.a + bd.a_off);
+            const u32 *pb = (const u32 *)((uintptr_t)P.b + bd.b_off);
+            u32 *pc = (u32 *)((uintptr_t)P.c + bd.c_off);
+            if (w.kind == IT_SMALL) {
+                SmallDesc d;
+                d.a = pa;
+                d.b = pb;
+                d.c = pc;
+                d.za = bd.za;
+                d.zb = bd.zb;
+                d.n = bd.n;
+                d.logT = bd.logT;
+                d.k = bd.k;
+                d.steps = bd.steps;
+                d.nsteps = bd.nsteps;
+                d.prune = 1;
+                d.cscale = bd.cscale;
+                small_dispatch<A>(d, P.m, P.tw);
+            } else {
+                LargeDesc d;
+                d.a = pa;
+                d.b = pb;
+                d.c = pc;
+                d.wa = (u32 *)((uintptr_t)P.ws + bd.ws_off);
+                d.wb = d.wa + bd.g.k * bd.g.S;
+                d.za = bd.za;
+                d.zb = bd.zb;
+                d.n = bd.n;
+                d.g = bd.g;
+                d.steps = bd.steps;
+                d.nsteps = bd.nsteps;
+                d.prune = 1;
+                d.cscale = bd.cscale;
+                if (w.kind == IT_COLF) colf_body<A, C>(d, w.idx, w.opnd, P.m, P.tw);
+                else if (w.kind == IT_ROW) row_body<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
+                else coli_body<A, C>(d, w.idx, P.m, P.tw);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && (w.kind == IT_COLF || w.kind == IT_ROW)) {
+            __threadfence();
+            atomicAdd(P.counters + 2 * w.prod + (w.kind == IT_ROW ? 1 : 0), 1);
+        }
+    }
+}
+
+template <class A, int C>
+static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<int, int> occ;  // device -> blocks per SM
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = occ.find(dev);
+        if (it == occ.end()) {
+            e = cudaFuncSetAttribute(k_batch<A, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM_MAX);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A, C>, BATCH_THREADS, BATCH_SMEM_MAX);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) per_sm = 1;
+            occ[dev] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int grid = per_sm * sms;
+    if (grid > P.nitems) grid = P.nitems;
+    if (grid < 1) grid = 1;
+    *grid_out = grid;
+    k_batch<A, C><<<grid, BATCH_THREADS, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -1,0 +1,12 @@
+// batch_lazy.cu -- persistent batched kernel instantiated for the
+// lazy (p < 2^30) arithmetic regime.
+#include "batch_kernel.cuh"
+
+namespace pm {
+
+cudaError_t launch_batch_lazy(int C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
+    return C == 32 ? launch_batch_t<Arith<true>, 32>(P, smem, grid, st)
+                   : launch_batch_t<Arith<true>, 16>(P, smem, grid, st);
+}
+
+}  // namespace pm

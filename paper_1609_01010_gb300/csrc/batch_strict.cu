@@ -1,0 +1,12 @@
+// batch_strict.cu -- persistent batched kernel instantiated for the
+// word-bound (2^30 < p < 2^31) arithmetic regime.
+#include "batch_kernel.cuh"
+
+namespace pm {
+
+cudaError_t launch_batch_strict(int C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
+    return C == 32 ? launch_batch_t<Arith<false>, 32>(P, smem, grid, st)
+                   : launch_batch_t<Arith<false>, 16>(P, smem, grid, st);
+}
+
+}  // namespace pm

@@ -1,0 +1,618 @@
+// host.cu -- host runtime of the C ABI: primes and resident twiddle tables,
+// ITFT step lists, schedules, and the single-product / transform entry points.
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "host.h"
+#include "polymul.h"
+
+namespace pm {
+
+cudaError_t launch_build_tw(uint2 *fwd, uint2 *inv, int lmax, u32 p, const u32 *pw_lo, const u32 *pw_hi,
+                            cudaStream_t st);
+
+// ------------------------------------------------------------ host math
+u32 h_powmod(u64 b, u64 e, u32 p) {
+    u64 r = 1 % p;
+    b %= p;
+    while (e) {
+        if (e & 1) r = r * b % p;
+        b = b * b % p;
+        e >>= 1;
+    }
+    return (u32)r;
+}
+u32 h_invmod(u32 a, u32 p) { return h_powmod(a, (u64)p - 2, p); }
+uint2 shoup_pair(u32 w, u32 p) { return make_uint2(w, (u32)(((u64)w << 32) / p)); }
+
+static u32 pinv32(u32 p) {
+    u32 x = p;  // p*x = 1 mod 8 for odd p
+    for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+    return x;
+}
+
+static bool h_is_prime(u32 p) {
+    if (p < 2) return false;
+    if (p % 2 == 0) return p == 2;
+    for (u64 d = 3; d * d <= p; d += 2)
+        if (p % d == 0) return false;
+    return true;
+}
+
+static bool h_is_primitive_root(u32 g, u32 p) {
+    u32 n = p - 1;
+    for (u32 d = 2; (u64)d * d <= n; ++d) {
+        if (n % d == 0) {
+            if (h_powmod(g, (p - 1) / d, p) == 1) return false;
+            while (n % d == 0) n /= d;
+        }
+    }
+    if (n > 1 && h_powmod(g, (p - 1) / n, p) == 1) return false;
+    return true;
+}
+
+static u32 h_bitrev(u32 i, int bits) {
+    u32 r = 0;
+    for (int b = 0; b < bits; ++b) {
+        r = (r << 1) | (i & 1u);
+        i >>= 1;
+    }
+    return r;
+}
+
+int ceil_log2(int64_t n) {
+    int l = 0;
+    while (((int64_t)1 << l) < n) ++l;
+    return l;
+}
+
+static u32 default_root(u32 p) {
+    if (p == 469762049u) return 3;
+    if (p == 2013265921u) return 31;
+    for (u32 g = 2; g < p; ++g)
+        if (h_is_primitive_root(g, p)) return g;
+    return 0;
+}
+
+// ------------------------------------------------------------ prime registry
+static std::mutex g_mu;
+static std::map<std::tuple<int, u32, u32>, PrimeCtx *> g_primes;
+static std::map<u32, bool> g_prime_ok;
+
+int validate_prime(u32 p, u32 *root) {
+    if (p < 3 || (p & 1u) == 0 || p >= (1u << 31)) return POLY_EINVAL_PRIME;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_prime_ok.find(p);
+        if (it == g_prime_ok.end()) it = g_prime_ok.emplace(p, h_is_prime(p)).first;
+        if (!it->second) return POLY_EINVAL_PRIME;
+    }
+    if (*root == 0) *root = default_root(p);
+    if (*root == 0 || *root >= p || !h_is_primitive_root(*root, p)) return POLY_EINVAL_PRIME;
+    return POLY_OK;
+}
+
+static int build_tables(PrimeCtx *ctx, int lmax, cudaStream_t st) {
+    const u32 p = ctx->p;
+    const u32 psi = h_powmod(ctx->root, (u64)(p - 1) >> lmax, p);
+    std::vector<u32> lo(4096), hi(((size_t)1 << lmax) / 4096 + 2);
+    u64 x = 1;
+    for (size_t a = 0; a < lo.size(); ++a) {
+        lo[a] = (u32)x;
+        x = x * psi % p;
+    }
+    const u32 step = h_powmod(psi, 4096, p);
+    x = 1;
+    for (size_t b = 0; b < hi.size(); ++b) {
+        hi[b] = (u32)x;
+        x = x * step % p;
+    }
+    const size_t entries = (size_t)1 << lmax;
+    uint2 *fwd = nullptr, *inv = nullptr;
+    u32 *dlo = nullptr, *dhi = nullptr;
+    if (cudaMalloc(&fwd, entries * sizeof(uint2)) != cudaSuccess) return POLY_ENOMEM;
+    if (cudaMalloc(&inv, entries * sizeof(uint2)) != cudaSuccess) {
+        cudaFree(fwd);
+        return POLY_ENOMEM;
+    }
+    if (cudaMalloc(&dlo, lo.size() * 4) != cudaSuccess || cudaMalloc(&dhi, hi.size() * 4) != cudaSuccess) {
+        cudaFree(fwd);
+        cudaFree(inv);
+        if (dlo) cudaFree(dlo);
+        return POLY_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(dlo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dhi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_build_tw(fwd, inv, lmax, p, dlo, dhi, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dlo);
+    cudaFree(dhi);
+    if (e != cudaSuccess) {
+        cudaFree(fwd);
+        cudaFree(inv);
+        return POLY_ECUDA;
+    }
+    // Kernels already queued may still read the old tables: keep them alive.
+    if (ctx->fwd) ctx->retired.push_back(const_cast<uint2 *>(ctx->tw.fwd));
+    if (ctx->inv) ctx->retired.push_back(const_cast<uint2 *>(ctx->tw.inv));
+    ctx->fwd = fwd;
+    ctx->inv = inv;
+    ctx->tw.fwd = fwd;
+    ctx->tw.inv = inv;
+    ctx->tw.lmax = lmax;
+    return POLY_OK;
+}
+
+int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st) {
+    int rc = validate_prime(p, &root);
+    if (rc) return rc;
+    const int v2 = __builtin_ctz(p - 1);
+    if (need_l > v2 || need_l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLY_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_tuple(dev, p, root);
+    auto it = g_primes.find(key);
+    PrimeCtx *ctx;
+    if (it == g_primes.end()) {
+        ctx = new PrimeCtx();
+        ctx->p = p;
+        ctx->root = root;
+        ctx->v2 = v2;
+        ctx->lazy = p < (1u << 30);
+        ctx->m.p = p;
+        ctx->m.pinv = pinv32(p);
+        ctx->tw = TwTables{nullptr, nullptr, 0};
+        g_primes[key] = ctx;
+    } else {
+        ctx = it->second;
+    }
+    int want = need_l < 16 ? 16 : need_l;
+    if (want > v2) want = v2;
+    if (ctx->tw.lmax < need_l || ctx->tw.fwd == nullptr) {
+        rc = build_tables(ctx, want, st);
+        if (rc) return rc;
+    }
+    *out = ctx;
+    return POLY_OK;
+}
+
+// ------------------------------------------------------------ ITFT steps
+// ITFT of node (s, i) of size M (rows [base, base+M)) from its first k leaves,
+// with the coefficients at rows >= k known (all zero when `zero`).  The node
+// splits x^M - r^2 into x^h - r (left, rows [base, base+h)) and x^h + r
+// (right); left coefficients are c_j + r c_{j+h}, right ones c_j - r c_{j+h}.
+//   k >= h: invert the left child fully (giving h times its coefficients);
+//           for j >= m = k-h the upper c_{j+h} are known, so c_j and the right
+//           child's coefficient c_j - r c_{j+h} follow (PRE_RIGHT); recurse on
+//           the right child with m leaves; combine the halves (POST_RIGHT).
+//   k <  h: the left child's coefficients for j >= k are known (PRE_LEFT),
+//           recurse on it, then c_j = lo_j - r c_{j+h} (POST_LEFT).
+// Every step keeps the scale of its inputs, except a top-level node with all
+// M leaves, which is one unscaled full inverse (M times the coefficients).
+static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool zero, bool top,
+                      std::vector<ItftStep> &out) {
+    const u32 p = ctx->p;
+    if (k == 0) return;
+    ItftStep st{};
+    if (k == M) {
+        st.kind = ST_FULL;
+        st.s = s;
+        st.i = i;
+        st.base = base;
+        st.h = M;
+        out.push_back(st);
+        return;
+    }
+    const int h = M / 2;
+    const u32 psi = h_powmod(ctx->root, (u64)(p - 1) >> (s + 1), p);
+    const u32 rev = h_bitrev(i, s);
+    const u32 r = h_powmod(psi, rev, p);
+    st.s = s;
+    st.i = i;
+    st.base = base;
+    st.h = h;
+    st.r = shoup_pair(r, p);
+    st.hinv = shoup_pair(h_invmod((u32)(h % p), p), p);
+    st.inv2 = shoup_pair(h_invmod(2, p), p);
+    st.i2r = shoup_pair(h_invmod((u32)((u64)2 * r % p), p), p);
+    if (k >= h) {
+        const int m = k - h;
+        ItftStep f{};
+        f.kind = ST_FULL;
+        f.s = s + 1;
+        f.i = 2 * i;
+        f.base = base;
+        f.h = h;
+        out.push_back(f);
+        st.kind = ST_PRE_RIGHT;
+        st.m = m;
+        st.zero = zero ? 1 : 0;
+        out.push_back(st);
+        steps_rec(ctx, s + 1, 2 * i + 1, base + h, h, m, false, false, out);
+        st.kind = ST_POST_RIGHT;
+        st.zero = 0;
+        out.push_back(st);
+    } else {
+        st.m = k;
+        if (!zero) {
+            st.kind = ST_PRE_LEFT;
+            out.push_back(st);
+        }
+        steps_rec(ctx, s + 1, 2 * i, base, h, k, zero, false, out);
+        if (!zero) {
+            st.kind = ST_POST_LEFT;
+            out.push_back(st);
+        }
+    }
+    (void)top;
+}
+
+std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k) {
+    std::vector<ItftStep> out;
+    steps_rec(ctx, 0, 0, 0, (int)M, (int)k, true, true, out);
+    return out;
+}
+
+// Device copy of the step list for (T, k), cached per prime context.
+int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int *nsteps) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(T, k);
+    auto it = ctx->steps.find(key);
+    if (it != ctx->steps.end()) {
+        *d_steps = it->second.first;
+        *nsteps = it->second.second;
+        return POLY_OK;
+    }
+    std::vector<ItftStep> v = itft_steps(ctx, T, k);
+    ItftStep *d = nullptr;
+    if (cudaMalloc(&d, v.size() * sizeof(ItftStep) + 16) != cudaSuccess) return POLY_ENOMEM;
+    if (cudaMemcpy(d, v.data(), v.size() * sizeof(ItftStep), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return POLY_ECUDA;
+    }
+    ctx->steps[key] = std::make_pair((const ItftStep *)d, (int)v.size());
+    *d_steps = d;
+    *nsteps = (int)v.size();
+    return POLY_OK;
+}
+
+// ------------------------------------------------------------ schedules
+static std::mutex g_sched_mu;
+static std::map<int, Schedule> g_sched;  // autotuned, by log2 L
+
+Schedule default_schedule(int l) {
+    Schedule s;
+    if (l <= 15) s.sigma = 10;
+    else if (l <= 20) s.sigma = 11;
+    else if (l <= 22) s.sigma = 12;
+    else s.sigma = 13;
+    const int t = l - s.sigma;
+    s.C = t >= 9 ? 16 : 32;
+    if (t >= 11) s.C = 16;
+    return s;
+}
+
+bool schedule_valid(int l, Schedule s) {
+    if (s.sigma < 9 || s.sigma > 13 || s.sigma > l) return false;
+    if (s.C != 8 && s.C != 16 && s.C != 32) return false;
+    const int t = l - s.sigma;
+    if (t > 11) return false;
+    if (((int64_t)1 << t) * s.C * 4 > 160 * 1024) return false;
+    if (((int64_t)1 << s.sigma) < s.C) return false;
+    return true;
+}
+
+Schedule schedule_for(int l) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched.find(l);
+    if (it != g_sched.end() && schedule_valid(l, it->second)) return it->second;
+    return default_schedule(l);
+}
+
+void set_schedule(int l, Schedule s) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched[l] = s;
+}
+
+std::map<int, Schedule> all_schedules() {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    return g_sched;
+}
+
+Geometry make_geometry(int64_t n, int l, int sigma) {
+    Geometry g;
+    g.l = l;
+    g.L = (int64_t)1 << l;
+    g.sigma = sigma < l ? sigma : l;
+    g.S = (int64_t)1 << g.sigma;
+    g.t = l - g.sigma;
+    g.T = (int64_t)1 << g.t;
+    g.n = n;
+    g.k = (n + g.S - 1) / g.S;
+    return g;
+}
+
+uint2 scale_const(u32 p, u64 scale) {
+    const u32 r32 = (u32)((((u64)1) << 32) % p);
+    const u32 c = (u32)((u64)r32 * h_invmod((u32)(scale % p), p) % p);
+    return shoup_pair(c, p);
+}
+
+// ------------------------------------------------------------ products
+// Fills a product descriptor for the small (one CTA) path.
+int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                  SmallDesc *d) {
+    const int lp = l < SMALL_LOG_S ? SMALL_LOG_S : l;
+    const int logT = lp - SMALL_LOG_S;
+    const int64_t T = (int64_t)1 << logT, S = (int64_t)1 << SMALL_LOG_S;
+    const int64_t n = za + zb - 1;
+    const int64_t k = prune ? (n + S - 1) / S : T;
+    const ItftStep *st = nullptr;
+    int ns = 0;
+    int rc = get_steps(ctx, T, k, &st, &ns);
+    if (rc) return rc;
+    d->a = a;
+    d->b = b;
+    d->c = c;
+    d->za = za;
+    d->zb = zb;
+    d->n = n;
+    d->logT = logT;
+    d->k = (int32_t)k;
+    d->steps = st;
+    d->nsteps = ns;
+    d->prune = prune ? 1 : 0;
+    d->cscale = scale_const(ctx->p, (u64)S * (k == T ? T : 1));
+    return POLY_OK;
+}
+
+int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                  Schedule sch, LargeDesc *d) {
+    const int64_t n = za + zb - 1;
+    Geometry g = make_geometry(n, l, sch.sigma);
+    if (!prune) g.k = g.T;
+    const ItftStep *st = nullptr;
+    int ns = 0;
+    int rc = get_steps(ctx, g.T, g.k, &st, &ns);
+    if (rc) return rc;
+    d->a = a;
+    d->b = b;
+    d->c = c;
+    d->wa = d->wb = nullptr;
+    d->za = za;
+    d->zb = zb;
+    d->n = n;
+    d->g = g;
+    d->steps = st;
+    d->nsteps = ns;
+    d->prune = prune ? 1 : 0;
+    d->cscale = scale_const(ctx->p, (u64)g.S * (g.k == g.T ? (u64)g.T : 1));
+    return POLY_OK;
+}
+
+int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune) {
+    Geometry g = make_geometry(n, l, sch.sigma);
+    if (!prune) g.k = g.T;
+    return 2 * g.k * g.S;
+}
+
+int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                cudaStream_t st, u32 *workspace) {
+    if (!a || !b || !c) return POLY_ENULL;
+    PrimeCtx *ctx = nullptr;
+    // Small products run with L padded to at least 512 (the product does not
+    // depend on L), so their tables must reach depth 9.
+    const bool small = l <= SMALL_MAX_LOG_L;
+    const int need = (small && l < SMALL_LOG_S) ? SMALL_LOG_S : l;
+    int rc = get_prime(p, root, need, &ctx, st);
+    if (rc) return rc;
+    if (small) {
+        SmallDesc d;
+        rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d);
+        if (rc) return rc;
+        return launch_small(ctx->lazy, d.logT, nullptr, &d, 1, ctx->m, ctx->tw, st) == cudaSuccess ? POLY_OK
+                                                                                                    : POLY_ECUDA;
+    }
+    const Schedule sch = schedule_for(l);
+    LargeDesc d;
+    rc = prepare_large(ctx, a, za, b, zb, c, l, prune, sch, &d);
+    if (rc) return rc;
+    const size_t bytes = (size_t)2 * d.g.k * d.g.S * sizeof(u32);
+    u32 *ws = workspace;
+    if (!ws) {
+        if (cudaMallocAsync((void **)&ws, bytes, st) != cudaSuccess) return POLY_ENOMEM;
+    }
+    d.wa = ws;
+    d.wb = ws + d.g.k * d.g.S;
+    cudaError_t e = launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st);
+    if (!workspace) cudaFreeAsync(ws, st);
+    return e == cudaSuccess ? POLY_OK : POLY_ECUDA;
+}
+
+static void keep_pool_memory() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+// ================================================================ C ABI
+extern "C" {
+
+const char *polymul_strerror(int s) {
+    switch (s) {
+        case POLY_OK: return "ok";
+        case POLY_EINVAL_PRIME: return "p is not an odd prime below 2^31, or root is not a primitive root";
+        case POLY_ETOO_LONG: return "transform length exceeds the prime's 2-adic order or the library limit";
+        case POLY_ENULL: return "a required pointer is NULL";
+        case POLY_ENOMEM: return "allocation failed";
+        case POLY_ECUDA: return "a CUDA runtime call failed";
+        case POLY_ETIMEOUT: return "a bounded wait expired";
+        case POLY_EINVAL: return "argument out of range";
+        case POLY_EBUSY: return "request exceeds the server memory budget";
+        case POLY_ENOTFOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+const char *polymul_version(void) { return "gb300-polymul 0.1 (sm_103a)"; }
+
+int polymul_mod_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                      void *stream) {
+    if (!a || !b || !c) return POLY_ENULL;
+    if (da < 0 || db < 0) return POLY_EINVAL;
+    keep_pool_memory();
+    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    const int l = ceil_log2(n);
+    if (l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
+    return run_product(p, 0, a, za, b, zb, c, l, true, (cudaStream_t)stream, nullptr);
+}
+
+int polymul_mod(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c) {
+    int rc = polymul_mod_async(p, a, da, b, db, c, nullptr);
+    if (rc) return rc;
+    return cudaStreamSynchronize(nullptr) == cudaSuccess ? POLY_OK : POLY_ECUDA;
+}
+
+int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                             int64_t Lp, void *stream) {
+    if (!a || !b || !c) return POLY_ENULL;
+    if (da < 0 || db < 0) return POLY_EINVAL;
+    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    if (Lp < n || (Lp & (Lp - 1))) return POLY_EINVAL;
+    const int l = ceil_log2(Lp);
+    if (l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
+    keep_pool_memory();
+    return run_product(p, 0, a, za, b, zb, c, l, false, (cudaStream_t)stream, nullptr);
+}
+
+int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c) {
+    if (!a || !b || !c) return POLY_ENULL;
+    if (da < 0 || db < 0) return POLY_EINVAL;
+    keep_pool_memory();
+    static thread_local cudaStream_t st = nullptr;
+    static thread_local int st_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLY_ECUDA;
+    if (!st || st_dev != dev) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return POLY_ECUDA;
+        st_dev = dev;
+    }
+    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    u32 *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, (size_t)(za + zb + n) * 4, st) != cudaSuccess) return POLY_ENOMEM;
+    u32 *da_ = buf, *db_ = buf + za, *dc_ = buf + za + zb;
+    int rc = POLY_OK;
+    if (cudaMemcpyAsync(da_, a, (size_t)za * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(db_, b, (size_t)zb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = POLY_ECUDA;
+    if (!rc) rc = polymul_mod_async(p, da_, da, db_, db, dc_, st);
+    if (!rc && cudaMemcpyAsync(c, dc_, (size_t)n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = POLY_ECUDA;
+    cudaFreeAsync(buf, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
+    return rc;
+}
+
+// ---------------------------------------------------------------- TFT plans
+struct tft_plan {
+    uint32_t p, root;
+    int64_t z, n, L;
+    int l;
+    PrimeCtx *ctx;
+    std::vector<ItftStep> steps;  // element-level ITFT(L, n, n)
+};
+
+int tft_plan_create(uint32_t p, uint32_t root, int64_t z, int64_t n, tft_plan **out) {
+    if (!out) return POLY_ENULL;
+    *out = nullptr;
+    if (z < 1 || n < z) return POLY_EINVAL;
+    const int l = ceil_log2(n);
+    if (l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
+    int rc = validate_prime(p, &root);
+    if (rc) return rc;
+    PrimeCtx *ctx = nullptr;
+    rc = get_prime(p, root, l, &ctx, nullptr);
+    if (rc) return rc;
+    tft_plan *pl = new tft_plan();
+    pl->p = p;
+    pl->root = root;
+    pl->z = z;
+    pl->n = n;
+    pl->l = l;
+    pl->L = (int64_t)1 << l;
+    pl->ctx = ctx;
+    pl->steps = itft_steps(ctx, pl->L, n);
+    *out = pl;
+    return POLY_OK;
+}
+
+int64_t tft_plan_length(const tft_plan *plan) { return plan ? plan->L : 0; }
+
+void tft_plan_destroy(tft_plan *plan) { delete plan; }
+
+int tft_exec(const tft_plan *pl, const uint32_t *in, uint32_t *out, void *stream) {
+    if (!pl || !in || !out) return POLY_ENULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
+    PrimeCtx *ctx = pl->ctx;
+    u32 *x = nullptr;
+    if (cudaMallocAsync((void **)&x, (size_t)pl->L * 4, st) != cudaSuccess) return POLY_ENOMEM;
+    cudaError_t e = launch_copy_pad(in, pl->z, x, pl->L, st);
+    for (int s = 0; s < pl->l && e == cudaSuccess; ++s)
+        e = launch_fwd_level(ctx->lazy, x, pl->L, s, pl->n, pl->z, ctx->m, ctx->tw, st);
+    if (e == cudaSuccess) e = launch_finish(ctx->lazy, x, out, pl->n, make_uint2(0, 0), 0, ctx->m, st);
+    cudaFreeAsync(x, st);
+    return e == cudaSuccess ? POLY_OK : POLY_ECUDA;
+}
+
+int itft_exec(const tft_plan *pl, const uint32_t *in, uint32_t *out, int scale, void *stream) {
+    if (!pl || !in || !out) return POLY_ENULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
+    PrimeCtx *ctx = pl->ctx;
+    u32 *x = nullptr;
+    if (cudaMallocAsync((void **)&x, (size_t)pl->L * 4, st) != cudaSuccess) return POLY_ENOMEM;
+    cudaError_t e = launch_copy_pad(in, pl->n, x, pl->L, st);
+    for (size_t i = 0; i < pl->steps.size() && e == cudaSuccess; ++i) {
+        const ItftStep &sp = pl->steps[i];
+        if (sp.kind == ST_FULL) {
+            const int lm = ceil_log2(sp.h);
+            for (int s = sp.s + lm - 1; s >= sp.s && e == cudaSuccess; --s)
+                e = launch_inv_level(ctx->lazy, x, s, sp.base, sp.h, sp.s, sp.i, ctx->m, ctx->tw, st);
+        } else {
+            e = launch_step(ctx->lazy, sp, x, ctx->m, st);
+        }
+    }
+    // n == L: one unscaled full inverse (L times g); otherwise g itself.
+    const u32 p = pl->p;
+    const bool full = pl->n == pl->L;
+    uint2 sc = make_uint2(1, 0);
+    int apply = 0;
+    if (full && scale) {
+        sc = shoup_pair(h_invmod((u32)(pl->L % p), p), p);
+        apply = 1;
+    } else if (!full && !scale) {
+        sc = shoup_pair((u32)(pl->L % p), p);
+        apply = 1;
+    }
+    if (e == cudaSuccess) e = launch_finish(ctx->lazy, x, out, pl->n, sc, apply, ctx->m, st);
+    cudaFreeAsync(x, st);
+    return e == cudaSuccess ? POLY_OK : POLY_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,51 @@
+// host.h -- host-side runtime state shared by the C ABI translation units.
+#pragma once
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace pm {
+
+// Per (device, prime, primitive root): resident twiddle tables and cached
+// ITFT step lists.  Created on first use, never freed before process exit.
+struct PrimeCtx {
+    u32 p = 0, root = 0;
+    int v2 = 0;  // 2-adic order of p-1
+    bool lazy = false;
+    ModParams m{};
+    TwTables tw{};
+    uint2 *fwd = nullptr, *inv = nullptr;
+    std::vector<uint2 *> retired;
+    std::map<std::pair<int64_t, int64_t>, std::pair<const ItftStep *, int>> steps;
+};
+
+u32 h_powmod(u64 b, u64 e, u32 p);
+u32 h_invmod(u32 a, u32 p);
+uint2 shoup_pair(u32 w, u32 p);
+int ceil_log2(int64_t n);
+
+int validate_prime(u32 p, u32 *root);
+int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st);
+std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k);
+int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int *nsteps);
+
+Schedule default_schedule(int l);
+bool schedule_valid(int l, Schedule s);
+Schedule schedule_for(int l);
+void set_schedule(int l, Schedule s);
+std::map<int, Schedule> all_schedules();
+
+Geometry make_geometry(int64_t n, int l, int sigma);
+uint2 scale_const(u32 p, u64 scale);
+
+int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                  SmallDesc *d);
+int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                  Schedule sch, LargeDesc *d);
+int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune);
+int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
+                cudaStream_t st, u32 *workspace);
+
+}  // namespace pm

@@ -1,0 +1,392 @@
+// server.cu -- continuous-batching server for products of mixed sizes/primes.
+//
+// submit() queues a request and returns a ticket.  A scheduler thread admits
+// queued requests in arrival order while the bytes they hold (operands,
+// output and workspace) fit the memory budget, packs the admitted requests of
+// one prime into a work list and launches the persistent batched kernel on a
+// free stream.  Requests that arrive while launches are running are admitted
+// into the next launch on another stream as soon as budget and a stream are
+// free, so their work overlaps on the GPU.  A host callback enqueued after
+// each launch stamps its completion time; latency = completion - submit.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch.h"
+#include "polymul.h"
+
+namespace pm {
+
+static double now_us() {
+    using namespace std::chrono;
+    return duration_cast<duration<double, std::micro>>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Pinned staging per stream for one launch's work list (allocated at
+// creation: pinned allocations are not made while launches are in flight).
+constexpr size_t SRV_STAGE_BYTES = (size_t)32 << 20;
+
+struct SrvReq {
+    uint64_t ticket;
+    u32 p;
+    const u32 *a, *b;
+    u32 *c;
+    int64_t za, zb, n;
+    uint64_t bytes;
+    double t_submit;
+};
+
+struct SrvLaunch;
+
+struct SrvStream {
+    cudaStream_t st = nullptr;
+    bool busy = false;
+    char *pinned = nullptr;
+    size_t pinned_bytes = 0;
+};
+
+struct SrvLaunch {
+    void *srv;  // the owning polymul_server
+    int stream;
+    std::vector<uint64_t> tickets;
+    std::vector<double> t_submit;
+    uint64_t bytes = 0;
+    void *dbuf = nullptr;
+    int *status_dev = nullptr;
+    int *status_host = nullptr;
+    double t_done = 0;
+    bool finished = false;
+};
+
+}  // namespace pm
+
+using namespace pm;
+
+struct polymul_server {
+    size_t budget = 0;
+    int dev = 0;
+    std::vector<SrvStream> streams;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<SrvReq> pending;
+    std::map<uint64_t, int> state;  // 0 queued, 1 running, 2 done
+    std::map<uint64_t, int> result;
+    std::vector<SrvLaunch *> inflight;
+    std::vector<double> lat_us;
+    uint64_t in_use = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread th;
+    std::map<u32, PrimeCtx *> ctx;
+};
+
+namespace pm {
+
+static void CUDART_CB srv_done_cb(void *arg) {
+    SrvLaunch *L = (SrvLaunch *)arg;
+    polymul_server *s = (polymul_server *)L->srv;
+    std::lock_guard<std::mutex> lk(s->mu);
+    L->t_done = now_us();
+    L->finished = true;
+    s->cv.notify_all();
+}
+
+// Work-list bytes a request adds to a launch's staging area (upper bound).
+static size_t request_stage_bytes(int64_t n) {
+    const int l = ceil_log2(n);
+    size_t items = 1;
+    if (l > SMALL_MAX_LOG_L) {
+        const int64_t S = (int64_t)1 << BATCH_SIGMA;
+        items = (size_t)(3 * (S / 16) + ((n + S - 1) / S));
+    }
+    return sizeof(BatchDesc) + items * sizeof(WorkItem) + 2 * sizeof(int);
+}
+
+static uint64_t request_bytes(int64_t za, int64_t zb) {
+    const int64_t n = za + zb - 1;
+    uint64_t bytes = (uint64_t)(za + zb + n) * 4;
+    const int l = ceil_log2(n);
+    if (l > SMALL_MAX_LOG_L) bytes += (uint64_t)large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true) * 4;
+    return bytes;
+}
+
+// Packs `reqs` (one prime) into a work list and launches it on stream si.
+// Called with the server lock held.
+static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
+    PrimeCtx *ctx = s->ctx[reqs[0].p];
+    SrvStream &ss = s->streams[si];
+    const int64_t cnt = (int64_t)reqs.size();
+    std::vector<int64_t> za(cnt), zb(cnt);
+    std::vector<uint64_t> ao(cnt), bo(cnt), co(cnt);
+    int max_l = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+        za[i] = reqs[i].za;
+        zb[i] = reqs[i].zb;
+        ao[i] = (uint64_t)(uintptr_t)reqs[i].a;
+        bo[i] = (uint64_t)(uintptr_t)reqs[i].b;
+        co[i] = (uint64_t)(uintptr_t)reqs[i].c;
+        max_l = std::max(max_l, ceil_log2(reqs[i].n));
+    }
+    const int C = batch_tile_width(max_l);
+    std::vector<BatchDesc> descs;
+    std::vector<WorkItem> items;
+    uint64_t ws_bytes = 0;
+    size_t smem = 0;
+    int rc = build_worklist(ctx, cnt, za.data(), zb.data(), ao.data(), bo.data(), co.data(), C, descs, items,
+                            &ws_bytes, &smem);
+    if (rc) return rc;
+    const size_t d_bytes = descs.size() * sizeof(BatchDesc);
+    const size_t i_bytes = items.size() * sizeof(WorkItem);
+    const size_t c_bytes = (2 * cnt + 2) * sizeof(int);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t stage = up(d_bytes) + up(i_bytes) + up(c_bytes);
+    const size_t total = stage + up(ws_bytes);
+    if (ss.pinned_bytes < stage + 256) return POLY_ENOMEM;  // admission keeps launches within the staging area
+    char *h = ss.pinned;
+    memcpy(h, descs.data(), d_bytes);
+    memcpy(h + up(d_bytes), items.data(), i_bytes);
+    memset(h + up(d_bytes) + up(i_bytes), 0, c_bytes);
+    char *dbuf = nullptr;
+    if (cudaMallocAsync((void **)&dbuf, total, ss.st) != cudaSuccess) return POLY_ENOMEM;
+    if (cudaMemcpyAsync(dbuf, h, stage, cudaMemcpyHostToDevice, ss.st) != cudaSuccess) return POLY_ECUDA;
+    BatchParams P;
+    P.a = nullptr;
+    P.b = nullptr;
+    P.c = nullptr;
+    P.ws = (u32 *)(dbuf + stage);
+    P.descs = (const BatchDesc *)dbuf;
+    P.items = (const WorkItem *)(dbuf + up(d_bytes));
+    P.nitems = (int)items.size();
+    P.counters = (int *)(dbuf + up(d_bytes) + up(i_bytes));
+    P.head = P.counters + 2 * cnt;
+    P.status = P.counters + 2 * cnt + 1;
+    P.m = ctx->m;
+    P.tw = ctx->tw;
+    P.spin_limit = BATCH_SPIN_LIMIT;
+    int grid = 0;
+    if (launch_batch(ctx->lazy, C, P, smem, &grid, ss.st) != cudaSuccess) return POLY_ECUDA;
+    SrvLaunch *L = new SrvLaunch();
+    L->srv = (void *)s;
+    L->stream = si;
+    L->dbuf = dbuf;
+    L->status_dev = P.status;
+    for (auto &r : reqs) {
+        L->tickets.push_back(r.ticket);
+        L->t_submit.push_back(r.t_submit);
+        L->bytes += r.bytes;
+        s->state[r.ticket] = 1;
+    }
+    // status word back to host memory (pinned, behind the kernel on the stream)
+    L->status_host = (int *)(h + stage);
+    if (cudaMemcpyAsync(L->status_host, P.status, sizeof(int), cudaMemcpyDeviceToHost, ss.st) != cudaSuccess)
+        return POLY_ECUDA;
+    if (cudaLaunchHostFunc(ss.st, srv_done_cb, L) != cudaSuccess) return POLY_ECUDA;
+    ss.busy = true;
+    s->inflight.push_back(L);
+    return POLY_OK;
+}
+
+static void srv_loop(polymul_server *s) {
+    cudaSetDevice(s->dev);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        // retire finished launches
+        for (size_t i = 0; i < s->inflight.size();) {
+            SrvLaunch *L = s->inflight[i];
+            if (!L->finished) {
+                ++i;
+                continue;
+            }
+            const int st = *L->status_host;
+            for (size_t j = 0; j < L->tickets.size(); ++j) {
+                s->state[L->tickets[j]] = 2;
+                s->result[L->tickets[j]] = st;
+                s->lat_us.push_back(L->t_done - L->t_submit[j]);
+            }
+            s->in_use -= L->bytes;
+            cudaFreeAsync(L->dbuf, s->streams[L->stream].st);
+            s->streams[L->stream].busy = false;
+            delete L;
+            s->inflight.erase(s->inflight.begin() + i);
+            s->cv.notify_all();
+        }
+        // admit and launch
+        bool launched = false;
+        for (size_t si = 0; si < s->streams.size() && !s->pending.empty(); ++si) {
+            if (s->streams[si].busy) continue;
+            const u32 p = s->pending.front().p;
+            std::vector<SrvReq> take;
+            uint64_t bytes = 0;
+            size_t staged = 4096;
+            for (auto it = s->pending.begin(); it != s->pending.end() && take.size() < 8192;) {
+                if (it->p != p) {
+                    ++it;
+                    continue;
+                }
+                if (s->in_use + bytes + it->bytes > s->budget) break;
+                const size_t sb = request_stage_bytes(it->n) + 1024;
+                if (staged + sb > s->streams[si].pinned_bytes) break;
+                staged += sb;
+                bytes += it->bytes;
+                take.push_back(*it);
+                it = s->pending.erase(it);
+            }
+            if (take.empty()) break;
+            s->in_use += bytes;
+            int rc = srv_launch(s, (int)si, take);
+            if (rc) {
+                s->in_use -= bytes;
+                for (auto &r : take) {
+                    s->state[r.ticket] = 2;
+                    s->result[r.ticket] = rc;
+                }
+                s->cv.notify_all();
+            }
+            launched = true;
+        }
+        if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+        if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+}  // namespace pm
+
+extern "C" {
+
+int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server **out) {
+    if (!out) return POLY_ENULL;
+    *out = nullptr;
+    if (mem_budget_bytes == 0 || n_streams < 1 || n_streams > 64) return POLY_EINVAL;
+    polymul_server *s = new polymul_server();
+    s->budget = mem_budget_bytes;
+    if (cudaGetDevice(&s->dev) != cudaSuccess) {
+        delete s;
+        return POLY_ECUDA;
+    }
+    const int max_l = BATCH_SIGMA + LARGE_MAX_LOG_T;
+    for (u32 p : {469762049u, 2013265921u}) {
+        PrimeCtx *c = nullptr;
+        int rc = get_prime(p, 0, max_l, &c, nullptr);
+        if (rc) {
+            delete s;
+            return rc;
+        }
+        s->ctx[p] = c;
+        // step lists for every (T, k) the server can meet are built on demand;
+        // the small-path lists are made resident now.
+        for (int logT = 0; logT <= SMALL_MAX_LOG_T; ++logT)
+            for (int64_t k = 1; k <= ((int64_t)1 << logT); ++k) {
+                const ItftStep *st;
+                int ns;
+                get_steps(c, (int64_t)1 << logT, k, &st, &ns);
+            }
+    }
+    s->streams.resize(n_streams);
+    for (auto &ss : s->streams) {
+        if (cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return POLY_ECUDA;
+        }
+        ss.pinned_bytes = SRV_STAGE_BYTES;
+        if (cudaMallocHost(&ss.pinned, ss.pinned_bytes) != cudaSuccess) {
+            ss.pinned = nullptr;
+            delete s;
+            return POLY_ENOMEM;
+        }
+    }
+    s->th = std::thread(srv_loop, s);
+    *out = s;
+    return POLY_OK;
+}
+
+int polymul_server_submit(polymul_server *s, uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                          uint32_t *c, uint64_t *ticket) {
+    if (!s || !a || !b || !c || !ticket) return POLY_ENULL;
+    if (da < 0 || db < 0) return POLY_EINVAL;
+    if (s->ctx.find(p) == s->ctx.end()) return POLY_EINVAL_PRIME;
+    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    if (ceil_log2(n) > BATCH_SIGMA + LARGE_MAX_LOG_T) return POLY_ETOO_LONG;
+    const uint64_t bytes = request_bytes(za, zb);
+    if (bytes > s->budget) return POLY_EBUSY;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return POLY_EINVAL;
+    SrvReq r{s->next_ticket++, p, a, b, c, za, zb, n, bytes, now_us()};
+    s->state[r.ticket] = 0;
+    s->pending.push_back(r);
+    *ticket = r.ticket;
+    s->cv.notify_all();
+    return POLY_OK;
+}
+
+int polymul_server_poll(polymul_server *s, uint64_t ticket, int *done) {
+    if (!s || !done) return POLY_ENULL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->state.find(ticket);
+    if (it == s->state.end()) return POLY_ENOTFOUND;
+    *done = it->second == 2;
+    return *done ? s->result[ticket] : POLY_OK;
+}
+
+int polymul_server_wait(polymul_server *s, uint64_t ticket, int64_t timeout_ms) {
+    if (!s) return POLY_ENULL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->state.find(ticket);
+    if (it == s->state.end()) return POLY_ENOTFOUND;
+    const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return s->state[ticket] == 2; });
+    if (!ok) return POLY_ETIMEOUT;
+    return s->result[ticket];
+}
+
+int polymul_server_stats(polymul_server *s, double *out6) {
+    if (!s || !out6) return POLY_ENULL;
+    std::vector<double> v;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        v = s->lat_us;
+    }
+    for (int i = 0; i < 6; ++i) out6[i] = 0;
+    if (v.empty()) return POLY_OK;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double q) {
+        size_t i = (size_t)(q * (double)(v.size() - 1) + 0.5);
+        return v[std::min(i, v.size() - 1)];
+    };
+    double sum = 0;
+    for (double x : v) sum += x;
+    out6[0] = (double)v.size();
+    out6[1] = pct(0.50);
+    out6[2] = pct(0.90);
+    out6[3] = pct(0.99);
+    out6[4] = v.back();
+    out6[5] = sum / (double)v.size();
+    return POLY_OK;
+}
+
+int polymul_server_destroy(polymul_server *s) {
+    if (!s) return POLY_ENULL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv.notify_all();
+    }
+    if (s->th.joinable()) s->th.join();
+    for (auto &ss : s->streams) {
+        if (ss.st) {
+            cudaStreamSynchronize(ss.st);
+            cudaStreamDestroy(ss.st);
+        }
+        if (ss.pinned) cudaFreeHost(ss.pinned);
+    }
+    delete s;
+    return POLY_OK;
+}
+
+}  // extern "C"

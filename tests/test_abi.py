@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every entry point include/polymul.h
+declares (no GPU and no compute call needed), and the host-side argument
+checks that run before any CUDA call behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "polymul.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1609_01010_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("polymul_mod", "polymul_mod_async", "tft_plan_create", "tft_exec", "itft_exec",
+                     "tft_plan_destroy", "polymul_mod_batched", "polymul_server_create",
+                     "polymul_server_submit", "polymul_server_poll", "polymul_server_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_symbol(lib):
+    from paper_1609_01010_gb300 import binding
+    assert set(header_functions()) <= set(binding._SIGS)
+    binding.lib()  # loads, sets every signature
+
+
+def test_host_side_argument_checks(lib):
+    """Checks that return before any CUDA call (null pointers, bad sizes)."""
+    from paper_1609_01010_gb300 import binding as B
+    L = B.lib()
+    POLY_ENULL, POLY_EINVAL = -3, -7
+    assert L.polymul_mod(469762049, None, 3, None, 3, None) == POLY_ENULL
+    assert L.polymul_mod_async(469762049, 16, -1, 16, 3, 16, None) == POLY_EINVAL
+    assert L.polymul_mod_padded_async(469762049, 16, 3, 16, 3, 16, 6, None) == POLY_EINVAL  # Lp not a power of 2
+    assert L.polymul_mod_padded_async(469762049, 16, 3, 16, 3, 16, 4, None) == POLY_EINVAL  # Lp < n
+    h = ctypes.c_void_p()
+    assert L.tft_plan_create(469762049, 0, 0, 5, ctypes.byref(h)) == POLY_EINVAL
+    assert L.tft_plan_create(469762049, 0, 6, 5, ctypes.byref(h)) == POLY_EINVAL
+    assert L.polymul_strerror(-6).decode().startswith("a bounded wait")
+    assert b"sm_103a" in L.polymul_version()
