@@ -59,6 +59,9 @@ extern "C" {
 /* Human-readable text for a status code (static storage). */
 const char *polymul_strerror(int status);
 
+/* Text of the last failing CUDA call made by this thread ("" if none). */
+const char *polymul_last_error(void);
+
 /* Library version string. */
 const char *polymul_version(void);
 
@@ -87,6 +90,17 @@ int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const ui
  * synchronous.
  */
 int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
+
+/*
+ * Measurement helpers.  Between polymul_profile_begin and polymul_profile_end
+ * every single-product call records CUDA events around its kernels on its
+ * stream.  polymul_profile_end synchronises those events and returns the
+ * summed device time in milliseconds and the number of launches per kernel:
+ * index 0 the one-CTA product kernel (L <= 8192), 1 the TFT column stage,
+ * 2 the row stage (forward, pointwise, inverse), 3 the ITFT column stage.
+ */
+int polymul_profile_begin(void);
+int polymul_profile_end(double *ms4, int64_t *launches4);
 
 /* ---------------------------------------------------------------- TFT plans */
 typedef struct tft_plan tft_plan;
@@ -143,6 +157,17 @@ int polymul_batch_exec_nograph(polymul_batch *batch, const uint32_t *a, const ui
 int polymul_batch_status(polymul_batch *batch);
 
 void polymul_batch_destroy(polymul_batch *batch);
+
+/*
+ * Test hook for the bounded waits: removes the first work item of `kind`
+ * (0 one-CTA product, 1 column item, 2 row item, 3 ITFT column item) from the
+ * batch's device work list and sets the wait limit to spin_limit polls of
+ * ~128 ns.  The next exec then has an item whose wait cannot be met; it must
+ * return POLY_ETIMEOUT through polymul_batch_status, not hang.  kind < 0
+ * restores the list and the default limit.  Use only on a non-graph exec
+ * (polymul_batch_exec_nograph).
+ */
+int polymul_batch_test_withhold(polymul_batch *batch, int kind, long long spin_limit);
 
 /*
  * One-shot convenience: create, exec and destroy (synchronous on `stream`).

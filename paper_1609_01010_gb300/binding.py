@@ -34,10 +34,13 @@ class PolymulError(RuntimeError):
 _SIGS = {
     "polymul_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "polymul_version": (ctypes.c_char_p, []),
+    "polymul_last_error": (ctypes.c_char_p, []),
     "polymul_mod": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
     "polymul_mod_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_mod_padded_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_mod_host": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
+    "polymul_profile_begin": (ctypes.c_int, []),
+    "polymul_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), I64P]),
     "tft_plan_create": (ctypes.c_int, [u32, u32, i64, i64, ctypes.POINTER(vp)]),
     "tft_plan_length": (i64, [vp]),
     "tft_exec": (ctypes.c_int, [vp, vp, vp, vp]),
@@ -48,6 +51,7 @@ _SIGS = {
     "polymul_batch_exec_nograph": (ctypes.c_int, [vp, vp, vp, vp, vp]),
     "polymul_batch_status": (ctypes.c_int, [vp]),
     "polymul_batch_destroy": (None, [vp]),
+    "polymul_batch_test_withhold": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
     "polymul_mod_batched": (ctypes.c_int, [u32, i64, vp, I64P, vp, I64P, vp, I64P, vp]),
     "polymul_mod_batched_plain": (ctypes.c_int, [u32, i64, vp, I64P, vp, I64P, vp, I64P, vp]),
     "polymul_autotune": (ctypes.c_int, [u32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
@@ -87,7 +91,8 @@ def strerror(status: int) -> str:
 
 def _check(rc: int, what: str) -> None:
     if rc != 0:
-        raise PolymulError(rc, what)
+        detail = lib().polymul_last_error().decode() if rc == -5 else ""
+        raise PolymulError(rc, f"{what} {detail}".strip())
 
 
 def _ptr(x) -> int | None:
@@ -134,6 +139,18 @@ def polymul_mod_padded_async(p: int, a, da: int, b, db: int, c, Lp: int, stream=
 def polymul_mod_host(p: int, a, da: int, b, db: int, c) -> None:
     """Host buffers (numpy uint32 arrays or pinned torch CPU tensors)."""
     _check(lib().polymul_mod_host(p, _ptr(a), da, _ptr(b), db, _ptr(c)), "polymul_mod_host")
+
+
+def polymul_profile_begin() -> None:
+    _check(lib().polymul_profile_begin(), "polymul_profile_begin")
+
+
+def polymul_profile_end() -> tuple[list[float], list[int]]:
+    """(ms per kernel, launches per kernel) for [small, column TFT, rows, column ITFT]."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(lib().polymul_profile_end(ms, n), "polymul_profile_end")
+    return list(ms), list(n)
 
 
 # ------------------------------------------------------------ TFT plans
@@ -210,6 +227,10 @@ def polymul_batch_status(batch: int) -> int:
 
 def polymul_batch_destroy(batch: int) -> None:
     lib().polymul_batch_destroy(batch)
+
+
+def polymul_batch_test_withhold(batch: int, kind: int, spin_limit: int) -> None:
+    _check(lib().polymul_batch_test_withhold(batch, kind, spin_limit), "polymul_batch_test_withhold")
 
 
 def polymul_mod_batched(p: int, a, a_off, b, b_off, c, c_off, stream=None) -> None:

@@ -130,6 +130,8 @@ struct polymul_batch {
     cudaEvent_t last = nullptr;
     std::map<std::tuple<uintptr_t, uintptr_t, uintptr_t, uintptr_t>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
     int grid = 0;
+    long long spin_limit = BATCH_SPIN_LIMIT;
+    int withheld = 0;  // items dropped by polymul_batch_test_withhold
 };
 
 static void batch_free(polymul_batch *b) {
@@ -217,13 +219,13 @@ static BatchParams batch_params(polymul_batch *b, const uint32_t *a, const uint3
     P.ws = b->ws;
     P.descs = b->descs;
     P.items = b->items;
-    P.nitems = (int)b->h_items.size();
+    P.nitems = (int)b->h_items.size() - b->withheld;
     P.counters = b->ctrl;
     P.head = b->ctrl + 2 * b->count;
     P.status = b->ctrl + 2 * b->count + 1;
     P.m = b->ctx->m;
     P.tw = b->ctx->tw;
-    P.spin_limit = BATCH_SPIN_LIMIT;
+    P.spin_limit = b->spin_limit;
     return P;
 }
 
@@ -281,6 +283,31 @@ int polymul_batch_status(polymul_batch *b) {
 void polymul_batch_destroy(polymul_batch *b) {
     if (b && b->last) cudaEventSynchronize(b->last);
     batch_free(b);
+}
+
+int polymul_batch_test_withhold(polymul_batch *b, int kind, long long spin_limit) {
+    if (!b) return POLY_ENULL;
+    if (kind < 0) {  // restore
+        b->spin_limit = BATCH_SPIN_LIMIT;
+        b->withheld = 0;
+        return cudaMemcpy(b->items, b->h_items.data(), b->h_items.size() * sizeof(WorkItem),
+                          cudaMemcpyHostToDevice) == cudaSuccess
+                   ? POLY_OK
+                   : POLY_ECUDA;
+    }
+    // Drop the first item of `kind` from the device work list (the last item
+    // moves into its place, so the list shrinks by one).
+    std::vector<WorkItem> v = b->h_items;
+    size_t i = 0;
+    while (i < v.size() && v[i].kind != kind) ++i;
+    if (i == v.size()) return POLY_EINVAL;
+    v.erase(v.begin() + i);
+    v.push_back(WorkItem{-1, 0, 0, 0});  // padding entry past nitems, never taken
+    b->spin_limit = spin_limit;
+    if (cudaMemcpy(b->items, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return POLY_ECUDA;
+    b->withheld = 1;
+    return POLY_OK;
 }
 
 int polymul_mod_batched(uint32_t p, int64_t count, const uint32_t *a, const int64_t *a_off, const uint32_t *b,

@@ -81,11 +81,10 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchParams P) {
                 else coli_body<A, C>(d, w.idx, P.m, P.tw);
             }
         }
+        __threadfence();  // each thread's outputs visible device-wide before the signal
         __syncthreads();
-        if (threadIdx.x == 0 && (w.kind == IT_COLF || w.kind == IT_ROW)) {
-            __threadfence();
+        if (threadIdx.x == 0 && (w.kind == IT_COLF || w.kind == IT_ROW))
             atomicAdd(P.counters + 2 * w.prod + (w.kind == IT_ROW ? 1 : 0), 1);
-        }
     }
 }
 

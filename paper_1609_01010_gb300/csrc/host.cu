@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -15,6 +16,13 @@ namespace pm {
 
 cudaError_t launch_build_tw(uint2 *fwd, uint2 *inv, int lmax, u32 p, const u32 *pw_lo, const u32 *pw_hi,
                             cudaStream_t st);
+
+static thread_local char g_last_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char *where) {
+    snprintf(g_last_err, sizeof g_last_err, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return POLY_ECUDA;
+}
 
 // ------------------------------------------------------------ host math
 u32 h_powmod(u64 b, u64 e, u32 p) {
@@ -270,12 +278,22 @@ int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int
         return POLY_OK;
     }
     std::vector<ItftStep> v = itft_steps(ctx, T, k);
-    ItftStep *d = nullptr;
-    if (cudaMalloc(&d, v.size() * sizeof(ItftStep) + 16) != cudaSuccess) return POLY_ENOMEM;
-    if (cudaMemcpy(d, v.data(), v.size() * sizeof(ItftStep), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d);
+    if (!ctx->upload && cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking) != cudaSuccess)
         return POLY_ECUDA;
+    if (ctx->arena_used + v.size() > ctx->arena_cap) {
+        const size_t cap = std::max<size_t>(v.size(), (size_t)1 << 15);
+        ItftStep *a = nullptr;
+        if (cudaMalloc(&a, cap * sizeof(ItftStep)) != cudaSuccess) return POLY_ENOMEM;
+        ctx->arenas.push_back(a);
+        ctx->arena_used = 0;
+        ctx->arena_cap = cap;
     }
+    ItftStep *d = ctx->arenas.back() + ctx->arena_used;
+    if (cudaMemcpyAsync(d, v.data(), v.size() * sizeof(ItftStep), cudaMemcpyHostToDevice, ctx->upload) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->upload) != cudaSuccess)
+        return POLY_ECUDA;
+    ctx->arena_used += v.size();
     ctx->steps[key] = std::make_pair((const ItftStep *)d, (int)v.size());
     *d_steps = d;
     *nsteps = (int)v.size();
@@ -342,6 +360,26 @@ uint2 scale_const(u32 p, u64 scale) {
     const u32 r32 = (u32)((((u64)1) << 32) % p);
     const u32 c = (u32)((u64)r32 * h_invmod((u32)(scale % p), p) % p);
     return shoup_pair(c, p);
+}
+
+// ------------------------------------------------------------ profiling
+// While enabled, every product records CUDA events around its kernels.
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+struct ProfRec {
+    int kind;  // 0 small, 1 large
+    cudaEvent_t ev[4];
+};
+static std::vector<ProfRec> g_prof;
+
+static cudaEvent_t *prof_events(int kind) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return nullptr;
+    ProfRec r;
+    r.kind = kind;
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&r.ev[i]);
+    g_prof.push_back(r);
+    return g_prof.back().ev;
 }
 
 // ------------------------------------------------------------ products
@@ -416,8 +454,11 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
         SmallDesc d;
         rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d);
         if (rc) return rc;
-        return launch_small(ctx->lazy, d.logT, nullptr, &d, 1, ctx->m, ctx->tw, st) == cudaSuccess ? POLY_OK
-                                                                                                    : POLY_ECUDA;
+        cudaEvent_t *ev = prof_events(0);
+        if (ev) cudaEventRecord(ev[0], st);
+        cudaError_t e = launch_small(ctx->lazy, d.logT, nullptr, &d, 1, ctx->m, ctx->tw, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        return e == cudaSuccess ? POLY_OK : cuda_fail(e, "one-CTA product launch");
     }
     const Schedule sch = schedule_for(l);
     LargeDesc d;
@@ -426,13 +467,20 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     const size_t bytes = (size_t)2 * d.g.k * d.g.S * sizeof(u32);
     u32 *ws = workspace;
     if (!ws) {
-        if (cudaMallocAsync((void **)&ws, bytes, st) != cudaSuccess) return POLY_ENOMEM;
+        cudaError_t e = cudaMallocAsync((void **)&ws, bytes, st);
+        if (e != cudaSuccess) {
+            cuda_fail(e, "workspace cudaMallocAsync");
+            return POLY_ENOMEM;
+        }
     }
     d.wa = ws;
     d.wb = ws + d.g.k * d.g.S;
-    cudaError_t e = launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st);
-    if (!workspace) cudaFreeAsync(ws, st);
-    return e == cudaSuccess ? POLY_OK : POLY_ECUDA;
+    cudaError_t e = launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st, prof_events(1));
+    if (!workspace) {
+        cudaError_t ef = cudaFreeAsync(ws, st);
+        if (e == cudaSuccess) e = ef;
+    }
+    return e == cudaSuccess ? POLY_OK : cuda_fail(e, "three-kernel product launch");
 }
 
 static void keep_pool_memory() {
@@ -444,6 +492,7 @@ static void keep_pool_memory() {
             uint64_t thr = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
+        cudaGetLastError();  // an unsupported pool attribute must not surface at the next launch
     });
 }
 
@@ -471,6 +520,49 @@ const char *polymul_strerror(int s) {
 }
 
 const char *polymul_version(void) { return "gb300-polymul 0.1 (sm_103a)"; }
+
+const char *polymul_last_error(void) { return g_last_err; }
+
+int polymul_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = true;
+    return POLY_OK;
+}
+
+int polymul_profile_end(double *ms4, int64_t *launches4) {
+    if (!ms4 || !launches4) return POLY_ENULL;
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_on = false;
+        recs.swap(g_prof);
+    }
+    for (int i = 0; i < 4; ++i) {
+        ms4[i] = 0;
+        launches4[i] = 0;
+    }
+    int rc = POLY_OK;
+    for (auto &r : recs) {
+        float t[3] = {0, 0, 0};
+        const int nk = r.kind == 0 ? 1 : 3;
+        for (int j = 0; j < nk; ++j) {
+            if (cudaEventSynchronize(r.ev[j + 1]) != cudaSuccess ||
+                cudaEventElapsedTime(&t[j], r.ev[j], r.ev[j + 1]) != cudaSuccess)
+                rc = POLY_ECUDA;
+        }
+        if (r.kind == 0) {
+            ms4[0] += t[0];
+            launches4[0] += 1;
+        } else {
+            for (int j = 0; j < 3; ++j) {
+                ms4[1 + j] += t[j];
+                launches4[1 + j] += 1;
+            }
+        }
+        for (int j = 0; j < 4; ++j) cudaEventDestroy(r.ev[j]);
+    }
+    return rc;
+}
 
 int polymul_mod_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
                       void *stream) {

@@ -19,7 +19,16 @@ struct PrimeCtx {
     uint2 *fwd = nullptr, *inv = nullptr;
     std::vector<uint2 *> retired;
     std::map<std::pair<int64_t, int64_t>, std::pair<const ItftStep *, int>> steps;
+    // Step lists live in device arenas filled through a private stream, so
+    // building one never synchronises the device.
+    std::vector<ItftStep *> arenas;
+    size_t arena_used = 0, arena_cap = 0;
+    cudaStream_t upload = nullptr;
 };
+
+// Records the last failing CUDA call of this thread (see polymul_last_error)
+// and returns POLY_ECUDA.
+int cuda_fail(cudaError_t e, const char *where);
 
 u32 h_powmod(u64 b, u64 e, u32 p);
 u32 h_invmod(u32 a, u32 p);

@@ -76,26 +76,14 @@ struct Schedule {
     int C;      // column tile width
 };
 
-// Raises a kernel's dynamic shared-memory limit once per device (the
-// attribute is per function and device; setting it on every launch would
-// cost a driver call per product).
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device):
+// the attribute is per function and device, and setting it on every launch
+// would cost a driver call per product.
+cudaError_t ensure_smem_ptr(const void *kern, size_t bytes);
 template <typename K>
 inline cudaError_t ensure_smem(K kern, size_t bytes) {
-    static unsigned long long done[4] = {0, 0, 0, 0};  // one bit per device
-    static size_t set_to[256] = {0};
     if (bytes <= 48 * 1024) return cudaSuccess;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if ((done[dev >> 6] & bit) && set_to[dev] >= bytes) return cudaSuccess;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) {
-        done[dev >> 6] |= bit;
-        set_to[dev] = bytes;
-    }
-    return e;
+    return ensure_smem_ptr((const void *)kern, bytes);
 }
 
 // ------------------------------------------------------------ launchers
@@ -128,7 +116,10 @@ struct LargeDesc {
     int32_t prune;  // 0: compute every butterfly (the zero-padded comparator)
     uint2 cscale;
 };
-cudaError_t launch_large(bool lazy, const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st);
+// ev: NULL, or 4 events recorded before the column stage, after it, after
+// the row stage and after the ITFT column stage (profiling).
+cudaError_t launch_large(bool lazy, const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st,
+                         cudaEvent_t *ev = nullptr);
 
 // Generic per-level kernels (any L): used by tft_exec / itft_exec.
 cudaError_t launch_copy_pad(const uint32_t *in, int64_t z, uint32_t *x, int64_t L, cudaStream_t st);

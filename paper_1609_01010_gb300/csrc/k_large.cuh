@@ -66,8 +66,10 @@ static cudaError_t launch_rows(const LargeDesc &d, ModParams m, TwTables tw, cud
 }
 
 template <class A>
-static cudaError_t launch_large_t(const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st) {
+static cudaError_t launch_large_t(const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st,
+                                  cudaEvent_t *ev) {
     cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], st);
     switch (sch.C) {
         case 8: e = launch_cols<A, 8>(d, m, tw, st); break;
         case 16: e = launch_cols<A, 16>(d, m, tw, st); break;
@@ -75,6 +77,7 @@ static cudaError_t launch_large_t(const LargeDesc &d, Schedule sch, ModParams m,
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
     switch (d.g.sigma) {
         case 9: e = launch_rows<A, 9>(d, m, tw, st); break;
         case 10: e = launch_rows<A, 10>(d, m, tw, st); break;
@@ -84,11 +87,14 @@ static cudaError_t launch_large_t(const LargeDesc &d, Schedule sch, ModParams m,
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
     switch (sch.C) {
-        case 8: return launch_cols_inv<A, 8>(d, m, tw, st);
-        case 16: return launch_cols_inv<A, 16>(d, m, tw, st);
-        default: return launch_cols_inv<A, 32>(d, m, tw, st);
+        case 8: e = launch_cols_inv<A, 8>(d, m, tw, st); break;
+        case 16: e = launch_cols_inv<A, 16>(d, m, tw, st); break;
+        default: e = launch_cols_inv<A, 32>(d, m, tw, st); break;
     }
+    if (ev) cudaEventRecord(ev[3], st);
+    return e;
 }
 
 }  // namespace pm

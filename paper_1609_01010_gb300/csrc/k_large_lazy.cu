@@ -4,8 +4,9 @@
 
 namespace pm {
 
-cudaError_t launch_large_lazy(const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st) {
-    return launch_large_t<Arith<true>>(d, sch, m, tw, st);
+cudaError_t launch_large_lazy(const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st,
+                              cudaEvent_t *ev) {
+    return launch_large_t<Arith<true>>(d, sch, m, tw, st, ev);
 }
 
 }  // namespace pm

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -63,7 +64,7 @@ struct SrvLaunch {
     int *status_dev = nullptr;
     int *status_host = nullptr;
     double t_done = 0;
-    bool finished = false;
+    std::atomic<bool> finished{false};
 };
 
 }  // namespace pm
@@ -86,17 +87,30 @@ struct polymul_server {
     bool stop = false;
     std::thread th;
     std::map<u32, PrimeCtx *> ctx;
+    // Wake-ups of the scheduler (new request, finished launch, stop).  The
+    // host callback of a launch takes only this mutex, never `mu`, and the
+    // scheduler never holds `mu` across a CUDA call: a CUDA call that
+    // synchronises the device can then never wait on a blocked callback.
+    std::mutex wake_mu;
+    std::condition_variable wake_cv;
+    uint64_t wake_seq = 0;
 };
 
 namespace pm {
 
+static void srv_wake(polymul_server *s) {
+    {
+        std::lock_guard<std::mutex> lk(s->wake_mu);
+        ++s->wake_seq;
+    }
+    s->wake_cv.notify_all();
+}
+
 static void CUDART_CB srv_done_cb(void *arg) {
     SrvLaunch *L = (SrvLaunch *)arg;
-    polymul_server *s = (polymul_server *)L->srv;
-    std::lock_guard<std::mutex> lk(s->mu);
     L->t_done = now_us();
-    L->finished = true;
-    s->cv.notify_all();
+    L->finished.store(true, std::memory_order_release);
+    srv_wake((polymul_server *)L->srv);
 }
 
 // Work-list bytes a request adds to a launch's staging area (upper bound).
@@ -119,7 +133,7 @@ static uint64_t request_bytes(int64_t za, int64_t zb) {
 }
 
 // Packs `reqs` (one prime) into a work list and launches it on stream si.
-// Called with the server lock held.
+// Runs on the scheduler thread without the server lock.
 static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
     PrimeCtx *ctx = s->ctx[reqs[0].p];
     SrvStream &ss = s->streams[si];
@@ -182,7 +196,6 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
         L->tickets.push_back(r.ticket);
         L->t_submit.push_back(r.t_submit);
         L->bytes += r.bytes;
-        s->state[r.ticket] = 1;
     }
     // status word back to host memory (pinned, behind the kernel on the stream)
     L->status_host = (int *)(h + stage);
@@ -196,64 +209,86 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
 
 static void srv_loop(polymul_server *s) {
     cudaSetDevice(s->dev);
-    std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        // retire finished launches
+        uint64_t seq0;
+        {
+            std::lock_guard<std::mutex> lk(s->wake_mu);
+            seq0 = s->wake_seq;
+        }
+        bool progress = false;
+        // 1. retire finished launches (the in-flight list belongs to this thread)
         for (size_t i = 0; i < s->inflight.size();) {
             SrvLaunch *L = s->inflight[i];
-            if (!L->finished) {
+            if (!L->finished.load(std::memory_order_acquire)) {
                 ++i;
                 continue;
             }
             const int st = *L->status_host;
-            for (size_t j = 0; j < L->tickets.size(); ++j) {
-                s->state[L->tickets[j]] = 2;
-                s->result[L->tickets[j]] = st;
-                s->lat_us.push_back(L->t_done - L->t_submit[j]);
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (size_t j = 0; j < L->tickets.size(); ++j) {
+                    s->state[L->tickets[j]] = 2;
+                    s->result[L->tickets[j]] = st;
+                    s->lat_us.push_back(L->t_done - L->t_submit[j]);
+                }
+                s->in_use -= L->bytes;
             }
-            s->in_use -= L->bytes;
+            s->cv.notify_all();
             cudaFreeAsync(L->dbuf, s->streams[L->stream].st);
             s->streams[L->stream].busy = false;
             delete L;
             s->inflight.erase(s->inflight.begin() + i);
-            s->cv.notify_all();
+            progress = true;
         }
-        // admit and launch
-        bool launched = false;
-        for (size_t si = 0; si < s->streams.size() && !s->pending.empty(); ++si) {
+        // 2. admit queued requests onto free streams and launch them
+        for (size_t si = 0; si < s->streams.size(); ++si) {
             if (s->streams[si].busy) continue;
-            const u32 p = s->pending.front().p;
             std::vector<SrvReq> take;
             uint64_t bytes = 0;
-            size_t staged = 4096;
-            for (auto it = s->pending.begin(); it != s->pending.end() && take.size() < 8192;) {
-                if (it->p != p) {
-                    ++it;
-                    continue;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (s->pending.empty()) break;
+                const u32 p = s->pending.front().p;
+                size_t staged = 4096;
+                for (auto it = s->pending.begin(); it != s->pending.end() && take.size() < 8192;) {
+                    if (it->p != p) {
+                        ++it;
+                        continue;
+                    }
+                    if (s->in_use + bytes + it->bytes > s->budget) break;
+                    const size_t sb = request_stage_bytes(it->n) + 1024;
+                    if (staged + sb > s->streams[si].pinned_bytes) break;
+                    staged += sb;
+                    bytes += it->bytes;
+                    s->state[it->ticket] = 1;
+                    take.push_back(*it);
+                    it = s->pending.erase(it);
                 }
-                if (s->in_use + bytes + it->bytes > s->budget) break;
-                const size_t sb = request_stage_bytes(it->n) + 1024;
-                if (staged + sb > s->streams[si].pinned_bytes) break;
-                staged += sb;
-                bytes += it->bytes;
-                take.push_back(*it);
-                it = s->pending.erase(it);
+                s->in_use += bytes;
             }
             if (take.empty()) break;
-            s->in_use += bytes;
-            int rc = srv_launch(s, (int)si, take);
+            const int rc = srv_launch(s, (int)si, take);
             if (rc) {
-                s->in_use -= bytes;
-                for (auto &r : take) {
-                    s->state[r.ticket] = 2;
-                    s->result[r.ticket] = rc;
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->in_use -= bytes;
+                    for (auto &r : take) {
+                        s->state[r.ticket] = 2;
+                        s->result[r.ticket] = rc;
+                    }
                 }
                 s->cv.notify_all();
             }
-            launched = true;
+            progress = true;
         }
-        if (s->stop && s->pending.empty() && s->inflight.empty()) break;
-        if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(200));
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+        }
+        if (!progress) {
+            std::unique_lock<std::mutex> lk(s->wake_mu);
+            s->wake_cv.wait_for(lk, std::chrono::microseconds(500), [&] { return s->wake_seq != seq0; });
+        }
     }
 }
 
@@ -280,14 +315,16 @@ int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server
             return rc;
         }
         s->ctx[p] = c;
-        // step lists for every (T, k) the server can meet are built on demand;
-        // the small-path lists are made resident now.
+        // Step lists for every (T, k) a request can meet are made resident now,
+        // so admission never builds one while launches are in flight.
+        const ItftStep *st;
+        int ns;
         for (int logT = 0; logT <= SMALL_MAX_LOG_T; ++logT)
-            for (int64_t k = 1; k <= ((int64_t)1 << logT); ++k) {
-                const ItftStep *st;
-                int ns;
-                get_steps(c, (int64_t)1 << logT, k, &st, &ns);
-            }
+            for (int64_t k = 1; k <= ((int64_t)1 << logT); ++k) get_steps(c, (int64_t)1 << logT, k, &st, &ns);
+        for (int t = SMALL_MAX_LOG_L + 1 - BATCH_SIGMA; t <= LARGE_MAX_LOG_T; ++t) {
+            const int64_t T = (int64_t)1 << t;
+            for (int64_t k = T / 2 + 1; k <= T; ++k) get_steps(c, T, k, &st, &ns);
+        }
     }
     s->streams.resize(n_streams);
     for (auto &ss : s->streams) {
@@ -316,13 +353,15 @@ int polymul_server_submit(polymul_server *s, uint32_t p, const uint32_t *a, int6
     if (ceil_log2(n) > BATCH_SIGMA + LARGE_MAX_LOG_T) return POLY_ETOO_LONG;
     const uint64_t bytes = request_bytes(za, zb);
     if (bytes > s->budget) return POLY_EBUSY;
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) return POLY_EINVAL;
-    SrvReq r{s->next_ticket++, p, a, b, c, za, zb, n, bytes, now_us()};
-    s->state[r.ticket] = 0;
-    s->pending.push_back(r);
-    *ticket = r.ticket;
-    s->cv.notify_all();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return POLY_EINVAL;
+        SrvReq r{s->next_ticket++, p, a, b, c, za, zb, n, bytes, now_us()};
+        s->state[r.ticket] = 0;
+        s->pending.push_back(r);
+        *ticket = r.ticket;
+    }
+    srv_wake(s);
     return POLY_OK;
 }
 
@@ -375,8 +414,8 @@ int polymul_server_destroy(polymul_server *s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
-        s->cv.notify_all();
     }
+    srv_wake(s);
     if (s->th.joinable()) s->th.join();
     for (auto &ss : s->streams) {
         if (ss.st) {
