@@ -92,6 +92,34 @@ int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const ui
 int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
 
 /*
+ * Allocation-free product for callers that cannot let a library allocate
+ * device memory: applications that reserve all device memory up front in
+ * their own pool (a library cudaMalloc would fail or bypass their
+ * accounting), and latency-critical callers that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.  The paper has
+ * no counterpart; it is a deployment variant of polymul_mod_async.
+ *
+ * Same result as polymul_mod_async (a, b, c: device buffers of da+1, db+1,
+ * da+db+1 words), computed with the same kernels, but the three-kernel
+ * path's workspace is a 1 MiB static device array inside the library (and the
+ * twiddle tables and step lists it needs are static arrays too: about 5.5 MiB
+ * in total, held by every GPU that loads the library until the process
+ * exits).  This call never calls cudaMalloc, cudaFree or any other
+ * allocating routine.
+ *  - p must be 469762049 or 2013265921 (else POLY_EINVAL_PRIME).
+ *  - n = da+db+1 must not exceed 131072 = 2^17 (else POLY_ETOO_LONG).
+ *  - The first call on a device sets the static tables up (with that device
+ *    current, synchronising the legacy default stream); make it before any
+ *    stream capture.
+ *  - All calls share the one workspace, which keeps the last call's
+ *    contents (nothing in it needs to start at zero): calls whose work
+ *    overlaps on the GPU (e.g. on different streams) race and give wrong
+ *    results.  Serialise them on one stream.
+ */
+int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                              uint32_t *c, void *stream);
+
+/*
  * Measurement helpers.  Between polymul_profile_begin and polymul_profile_end
  * every single-product call records CUDA events around its kernels on its
  * stream.  polymul_profile_end synchronises those events and returns the

@@ -39,6 +39,7 @@ _SIGS = {
     "polymul_mod_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_mod_padded_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_mod_host": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
+    "polymul_mod_noalloc_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_profile_begin": (ctypes.c_int, []),
     "polymul_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), I64P]),
     "tft_plan_create": (ctypes.c_int, [u32, u32, i64, i64, ctypes.POINTER(vp)]),
@@ -134,6 +135,12 @@ def polymul_mod_async(p: int, a, da: int, b, db: int, c, stream=None) -> None:
 def polymul_mod_padded_async(p: int, a, da: int, b, db: int, c, Lp: int, stream=None) -> None:
     _check(lib().polymul_mod_padded_async(p, _ptr(a), da, _ptr(b), db, _ptr(c), Lp, _stream(stream)),
            "polymul_mod_padded_async")
+
+
+def polymul_mod_noalloc_async(p: int, a, da: int, b, db: int, c, stream=None) -> None:
+    """The allocation-free product (n <= 2^17; p = 469762049 or 2013265921)."""
+    _check(lib().polymul_mod_noalloc_async(p, _ptr(a), da, _ptr(b), db, _ptr(c), _stream(stream)),
+           "polymul_mod_noalloc_async")
 
 
 def polymul_mod_host(p: int, a, da: int, b, db: int, c) -> None:
