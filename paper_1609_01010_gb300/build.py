@@ -44,18 +44,33 @@ def _stale(target: str, sources: list[str]) -> bool:
     return any(os.path.getmtime(s) > t for s in sources)
 
 
+# Sources compiled once per variant (preprocessor defines), so their many
+# template instantiations build in parallel.
+def _variants() -> dict[str, list[tuple[str, list[str]]]]:
+    cols = []
+    for fwd in (1, 0):
+        for lazy in (1, 0):
+            for c in (8, 32, 128):
+                name = f"launch_col{'f' if fwd else 'i'}_{'lazy' if lazy else 'strict'}_c{c}"
+                cols.append((name, [f"-DPM_FWD={fwd}", f"-DPM_LAZY={lazy}", f"-DPM_C={c}", f"-DPM_COL_FN={name}"]))
+    return {"k_cols.cu": cols}
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
     cc = nvcc()
+    variants = _variants()
     jobs = []
     objs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + deps):
-            jobs.append([cc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+        base = os.path.basename(src)[:-3]
+        for tag, defs in variants.get(os.path.basename(src), [(None, [])]):
+            obj = os.path.join(BUILD, base + (f".{tag}" if tag else "") + ".o")
+            objs.append(obj)
+            if force or _stale(obj, [src] + deps):
+                jobs.append([cc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

@@ -73,7 +73,7 @@ int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path) 
         Schedule best{0, 0};
         float best_us = 1e30f;
         for (int sigma = 9; sigma <= 13; ++sigma)
-            for (int C : {8, 16, 32}) {
+            for (int C : {8, 32, 128}) {
                 Schedule s{sigma, C};
                 if (!schedule_valid(l, s)) continue;
                 const float us = time_schedule(ctx, l, s, a, b, c, ws, st, e0, e1);

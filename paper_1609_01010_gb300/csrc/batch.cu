@@ -73,7 +73,7 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
             d.ws_off = ws;
             ws += (uint64_t)2 * ld.g.k * ld.g.S * 4;
             smem = std::max(smem, (size_t)ld.g.T * C * 4);
-            smem = std::max(smem, (size_t)4 * ld.g.S * 4);
+            smem = std::max(smem, row_smem_bytes(BATCH_SIGMA));
             large.push_back({d.n, i});
         }
     }
@@ -101,12 +101,13 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
 }
 
 int batch_tile_width(int max_l) {
-    // Column tiles of the batch: T * C words of shared memory must fit the
-    // persistent CTA's budget.
+    // Column tiles of the batch (8, 32 or 128 columns) hold T * C words in
+    // the persistent CTA's shared memory; wide tiles for short columns keep
+    // each item near 8K words, so per-item overhead stays small.
     const int t = max_l - BATCH_SIGMA;
-    if (t >= 10) return 16;
-    Schedule s = schedule_for(max_l < 14 ? 14 : max_l);
-    return s.C == 32 ? 32 : 16;
+    if (t <= 6) return 128;
+    if (t <= 8) return 32;
+    return 8;
 }
 
 }  // namespace pm

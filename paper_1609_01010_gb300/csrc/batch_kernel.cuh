@@ -24,7 +24,7 @@ __device__ __forceinline__ bool wait_count(const int *ctr, int target, int *stat
 }
 
 template <class A, int C>
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchParams P) {
+__global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(BatchParams P) {
     __shared__ int s_item, s_ok;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.head, 1);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchParams P) {
                 d.prune = 1;
                 d.cscale = bd.cscale;
                 if (w.kind == IT_COLF) colf_body<A, C>(d, w.idx, w.opnd, P.m, P.tw);
-                else if (w.kind == IT_ROW) row_body<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
+                else if (w.kind == IT_ROW) row_body_ool<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
                 else coli_body<A, C>(d, w.idx, P.m, P.tw);
             }
         }

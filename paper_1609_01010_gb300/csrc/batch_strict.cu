@@ -5,8 +5,9 @@
 namespace pm {
 
 cudaError_t launch_batch_strict(int C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
-    return C == 32 ? launch_batch_t<Arith<false>, 32>(P, smem, grid, st)
-                   : launch_batch_t<Arith<false>, 16>(P, smem, grid, st);
+    if (C == 128) return launch_batch_t<Arith<false>, 128>(P, smem, grid, st);
+    if (C == 32) return launch_batch_t<Arith<false>, 32>(P, smem, grid, st);
+    return launch_batch_t<Arith<false>, 8>(P, smem, grid, st);
 }
 
 }  // namespace pm

@@ -22,15 +22,20 @@ __device__ __forceinline__ u32 *dyn_smem() {
 // One product with L = T * 512 <= 8192 (see k_small.cu).  Any blockDim that
 // is a multiple of 32; shared memory: 2 * T * 512 words.
 template <class A, int LOGT>
-__device__ __noinline__ void small_body(const SmallDesc &d, ModParams m, TwTables tw) {
+__device__ __forceinline__ void small_body(const SmallDesc &d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     constexpr int T = 1 << LOGT;
     constexpr int S = 1 << SMALL_LOG_S;
     u32 *sa = smem, *sb = smem + T * S;
     const u32 p = m.p;
     const int zba = (int)((d.za + S - 1) / S), zbb = (int)((d.zb + S - 1) / S);
-    col_fwd_tile<A, S>(sa, d.a, d.za, S, 0, T, LOGT, zba, d.k, d.prune != 0, tw.fwd, p);
-    col_fwd_tile<A, S>(sb, d.b, d.zb, S, 0, T, LOGT, zbb, d.k, d.prune != 0, tw.fwd, p);
+    ColFwdArgs X{sa, d.a, nullptr, d.za, 0u, SMALL_LOG_S, T, LOGT, zba, d.k, d.prune != 0, tw.fwd, p};
+    colf_tile<A, S, LAY_SWZ>(X, false);
+    X.sm = sb;
+    X.g = d.b;
+    X.z = d.zb;
+    X.zb = zbb;
+    colf_tile<A, S, LAY_SWZ>(X, false);
 
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int w = threadIdx.x >> 5; w < d.k; w += nw) {
@@ -43,85 +48,208 @@ __device__ __noinline__ void small_body(const SmallDesc &d, ModParams m, TwTable
         srow_inv<A, SMALL_LOG_S, NP - 1>(xa, sa + w * S, lane, LOGT, (u32)w, tw.inv, p);
     }
     __syncthreads();
-    col_itft_steps<A, S>(sa, d.steps, d.nsteps, tw.inv, p);
+    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p};
+    coli_steps<A, S, LAY_SWZ>(Y, d.steps, d.nsteps);
     for (int64_t e = threadIdx.x; e < d.n; e += blockDim.x) d.c[e] = A::to_canon(sa[swz((u32)e)], p);
     __syncthreads();
+}
+
+// Out-of-line copies for the persistent batched kernel (keeps it small;
+// the one-launch kernels inline the bodies).
+template <class A, int LOGT>
+__device__ __noinline__ void small_body_ool(const SmallDesc d, ModParams m, TwTables tw) {
+    small_body<A, LOGT>(d, m, tw);
 }
 
 template <class A>
 __device__ void small_dispatch(const SmallDesc &d, ModParams m, TwTables tw) {
     switch (d.logT) {
-        case 0: small_body<A, 0>(d, m, tw); break;
-        case 1: small_body<A, 1>(d, m, tw); break;
-        case 2: small_body<A, 2>(d, m, tw); break;
-        case 3: small_body<A, 3>(d, m, tw); break;
-        default: small_body<A, 4>(d, m, tw); break;
+        case 0: small_body_ool<A, 0>(d, m, tw); break;
+        case 1: small_body_ool<A, 1>(d, m, tw); break;
+        case 2: small_body_ool<A, 2>(d, m, tw); break;
+        case 3: small_body_ool<A, 3>(d, m, tw); break;
+        default: small_body_ool<A, 4>(d, m, tw); break;
     }
 }
 
 // ---------------------------------------------------------- large product
 // Column stage of operand `opnd` on column tile `tile` (C columns); writes
 // the k needed rows to the workspace.  Shared memory: T * C words.
-template <class A, int C>
-__device__ __noinline__ void colf_body(const LargeDesc &d, int tile, int opnd, ModParams m, TwTables tw) {
-    u32 *smem = dyn_smem();
+// Issues the cp.async copies of column tile `tile` of operand `opnd` (rows
+// r < T, columns c0..c0+C) into buf (LAY_TILE); entries at or past the
+// operand's length are written as zeros.  16-byte copies when the operand is
+// 16-byte aligned, 4-byte copies otherwise (packed batch operands).
+template <int C>
+__device__ __forceinline__ void colf_load(const LargeDesc &d, int tile, int opnd, u32 *buf) {
     const u32 *g = opnd ? d.b : d.a;
     const int64_t z = opnd ? d.zb : d.za;
-    u32 *W = opnd ? d.wb : d.wa;
+    const u32 c0 = (u32)tile * C;
+    const int logS = d.g.sigma;
+    const bool al = (((uintptr_t)g) & 15u) == 0;
+    constexpr int logCH = ilog2c(C) - 2;  // 4-word chunks per row
+    const int nch = (int)d.g.T << logCH;
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) {
+        const u32 r = (u32)i >> logCH, c = ((u32)i & ((1u << logCH) - 1u)) << 2;
+        u32 *dst = buf + col_elem_addr<C, LAY_TILE>(r, c);
+        const int64_t e = ((int64_t)r << logS) + c0 + c;
+        if (e >= z) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        } else if (al && e + 4 <= z) {
+            cp_async16(dst, g + e);
+        } else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (e + w < z) cp_async4(dst + w, g + e + w);
+                else dst[w] = 0u;
+            }
+        }
+    }
+}
+
+// Column stage of a tile already in buf; the last pass writes rows < k of
+// the workspace.  Ends with a barrier.
+template <class A, int C>
+__device__ __forceinline__ void colf_compute(const LargeDesc &d, int tile, int opnd, u32 *buf, ModParams m,
+                                          TwTables tw) {
+    const int64_t z = opnd ? d.zb : d.za;
     const int64_t S = d.g.S, c0 = (int64_t)tile * C;
     const int T = (int)d.g.T, t = d.g.t;
-    const int k = d.prune ? (int)d.g.k : T;
     int zb = z > c0 ? (int)((z - c0 + S - 1) / S) : 0;
     if (zb > T) zb = T;
-    col_fwd_tile<A, C>(smem, g, z, S, c0, T, t, zb, k, d.prune != 0, tw.fwd, m.p);
-    for (int tau = threadIdx.x; tau < k * C; tau += blockDim.x) {
-        const int r = tau / C, c = tau % C;
-        W[(int64_t)r * S + c0 + c] = smem[swz(r * C + c)];
+    const ColFwdArgs X{buf, nullptr, opnd ? d.wb : d.wa, z, (u32)c0, d.g.sigma, T, t, zb,
+                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p};
+    if (t == 0) {
+        for (int c = threadIdx.x; c < C; c += blockDim.x) X.W[c0 + c] = buf[col_elem_addr<C, LAY_TILE>(0, c)];
+        __syncthreads();
+        return;
     }
+    const int np = col_npass(t);
+    int s0 = 0;
+    for (int i = 0; i < np; ++i) {
+        const int R = col_pass_R(t, np, i);
+        if (i == np - 1) colf_pass_r<A, C, LAY_TILE, IO_SMEM, IO_GLOBAL>(R, X, s0);
+        else colf_pass_r<A, C, LAY_TILE, IO_SMEM, IO_SMEM>(R, X, s0);
+        __syncthreads();
+        s0 += R;
+    }
+}
+
+// Compile-time-shaped column stage of a loaded tile (TL = t levels).
+template <class A, int C, int TL>
+__device__ __forceinline__ void colf_compute_ct(const LargeDesc &d, int tile, int opnd, u32 *buf, ModParams m,
+                                             TwTables tw) {
+    const int64_t z = opnd ? d.zb : d.za;
+    const int64_t S = d.g.S, c0 = (int64_t)tile * C;
+    const int T = 1 << TL;
+    int zb = z > c0 ? (int)((z - c0 + S - 1) / S) : 0;
+    if (zb > T) zb = T;
+    const ColFwdArgs X{buf, nullptr, opnd ? d.wb : d.wa, z, (u32)c0, d.g.sigma, T, TL, zb,
+                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p};
+    colf_tile_ct<A, C, TL>(X);
+}
+
+// One column-stage item with a single buffer (the persistent batched kernel).
+template <class A, int C>
+__device__ __noinline__ void colf_body(const LargeDesc d, int tile, int opnd, ModParams m, TwTables tw) {
+    u32 *smem = dyn_smem();
+    colf_load<C>(d, tile, opnd, smem);
+    cp_async_wait_all();
     __syncthreads();
+    colf_compute<A, C>(d, tile, opnd, smem, m, tw);
 }
 
 // Row ib: remaining sigma levels of both operands, pointwise product,
-// unscaled inverse; result overwrites wa's row.  blockDim must be S/16;
-// shared memory: 4 * S words.
+// unscaled inverse; result overwrites wa's row.  blockDim must be S/16.
+// Shared memory: 2*S words of data + (S-1) twiddles (8 bytes each).
 template <class A, int SIGMA>
-__device__ __noinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m, TwTables tw) {
+__device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     constexpr int S = 1 << SIGMA;
     constexpr int NP = RowPlan<SIGMA, 0>::NP;
-    u32 *a0 = smem, *a1 = smem + S, *b0 = smem + 2 * S, *b1 = smem + 3 * S;
+    u32 *ba = smem, *bb = smem + S;
+    uint2 *twb = reinterpret_cast<uint2 *>(smem + 2 * S);
     const u32 tid = threadIdx.x;
     const u32 p = m.p;
     u32 *rowa = d.wa + (int64_t)ib * S;
-    const u32 *rowb = d.wb + (int64_t)ib * S;
+    stage_row<S>(ba, rowa);
+    stage_row<S>(bb, d.wb + (int64_t)ib * S);
+    stage_tw<SIGMA>(twb, tw.fwd, d.g.t, ib);
+    cp_async_wait_all();
+    __syncthreads();
     u32 xa[16], xb[16];
-    lrow_fwd<A, SIGMA, 0>(xa, rowa, a0, a1, tid, d.g.t, ib, tw.fwd, p);
-    lrow_fwd<A, SIGMA, 0>(xb, rowb, b0, b1, tid, d.g.t, ib, tw.fwd, p);
+    srow2_fwd<A, SIGMA, 0>(xa, xb, ba, bb, twb, tid, p);
 #pragma unroll
     for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], d.cscale, m);
-    lrow_inv<A, SIGMA, NP - 1>(xa, rowa, a0, a1, tid, d.g.t, ib, tw.inv, p);
+    __syncthreads();  // every thread is done with the forward twiddles
+    stage_tw<SIGMA>(twb, tw.inv, d.g.t, ib);
+    cp_async_wait_all();
+    __syncthreads();
+    srow2_inv<A, SIGMA, NP - 1>(xa, ba, rowa, twb, tid, p);
     __syncthreads();
 }
 
-// ITFT column stage of tile `tile` and the store of the first n outputs.
-// Shared memory: T * C words.
+template <class A, int SIGMA>
+__device__ __noinline__ void row_body_ool(const LargeDesc d, u32 ib, ModParams m, TwTables tw) {
+    row_body<A, SIGMA>(d, ib, m, tw);
+}
+
+// Issues the cp.async copies of the k needed workspace rows of tile `tile`.
+template <int C>
+__device__ __forceinline__ void coli_load(const LargeDesc &d, int tile, u32 *buf) {
+    const u32 c0 = (u32)tile * C;
+    constexpr int logCH = ilog2c(C) - 2;
+    const int nch = (int)d.g.k << logCH;
+    const int logS = d.g.sigma;
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) {
+        const u32 r = (u32)i >> logCH, c = ((u32)i & ((1u << logCH) - 1u)) << 2;
+        cp_async16(buf + col_elem_addr<C, LAY_TILE>(r, c), d.wa + ((int64_t)r << logS) + c0 + c);
+    }
+}
+
+// ITFT column stage of a tile already in buf, and the store of its part of
+// the first n outputs (reduced to [0, p)).  Ends with a barrier.
 template <class A, int C>
-__device__ __noinline__ void coli_body(const LargeDesc &d, int tile, ModParams m, TwTables tw) {
-    u32 *smem = dyn_smem();
-    const int64_t S = d.g.S, c0 = (int64_t)tile * C;
+__device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
+    const int64_t S = d.g.S;
+    const u32 c0 = (u32)tile * C;
     const int T = (int)d.g.T, k = (int)d.g.k;
-    for (int tau = threadIdx.x; tau < T * C; tau += blockDim.x) {
-        const int r = tau / C, c = tau % C;
-        smem[swz(r * C + c)] = r < k ? ld_cg(d.wa + (int64_t)r * S + c0 + c) : 0u;
+    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p};
+    if (d.g.t == 0) {
+        for (int c = threadIdx.x; c < C; c += blockDim.x)
+            if ((int64_t)(c0 + c) < d.n) d.c[c0 + c] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(0, c)], m.p);
+        __syncthreads();
+        return;
     }
-    __syncthreads();
-    col_itft_steps<A, C>(smem, d.steps, d.nsteps, tw.inv, m.p);
+    if (k == T) {  // no truncation: one unscaled full inverse, last pass to the output
+        coli_full<A, C, LAY_TILE>(X, 0, 0u, 0, d.g.t, false, true);
+        return;
+    }
+    coli_steps<A, C, LAY_TILE>(X, d.steps, d.nsteps);
     for (int tau = threadIdx.x; tau < k * C; tau += blockDim.x) {
-        const int r = tau / C, c = tau % C;
+        const u32 r = (u32)tau / C, c = (u32)tau % C;
         const int64_t e = (int64_t)r * S + c0 + c;
-        if (e < d.n) d.c[e] = A::to_canon(smem[swz(r * C + c)], m.p);
+        if (e < d.n) d.c[e] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(r, c)], m.p);
     }
     __syncthreads();
+}
+
+template <class A, int C, int TL>
+__device__ __forceinline__ void coli_compute_ct(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
+    if (d.g.k == d.g.T) {
+        const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p};
+        coli_full_ct<A, C, TL>(X);
+    } else {
+        coli_compute<A, C>(d, tile, buf, m, tw);
+    }
+}
+
+template <class A, int C>
+__device__ __noinline__ void coli_body(const LargeDesc d, int tile, ModParams m, TwTables tw) {
+    u32 *smem = dyn_smem();
+    coli_load<C>(d, tile, smem);
+    cp_async_wait_all();
+    __syncthreads();
+    coli_compute<A, C>(d, tile, smem, m, tw);
 }
 
 }  // namespace pm

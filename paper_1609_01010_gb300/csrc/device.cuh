@@ -21,11 +21,15 @@
 // support are zero, which makes whole tree levels plain copies, and nodes
 // whose leaves all lie beyond the k needed rows are skipped.
 #pragma once
+#include <type_traits>
+
 #include "internal.h"
 
 namespace pm {
 
 __device__ __forceinline__ u32 swz(u32 w) { return w ^ (((w >> 5) & 7u) << 2); }
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 
 // ----------------------------------------------------------------- groups
 // A group holds 2^R elements x[q] of one node at depth lev0 (node index
@@ -105,15 +109,29 @@ struct RowPlan {
     static constexpr int U0 = 4 * P;   // first sub-level of the pass
 };
 
+// G + q*(S>>R) with S>>R a multiple of 256 never carries into bits [7:5],
+// so swz(G + q*(S>>R)) = swz(G) + q*(S>>R): one swizzle per group.
 template <int R, int S>
 __device__ __forceinline__ void ld_str_s(const u32 *buf, u32 G, u32 *x) {
+    if constexpr ((S >> R) % 256 == 0) {
+        const u32 *b = buf + swz(G);
 #pragma unroll
-    for (int q = 0; q < (1 << R); ++q) x[q] = buf[swz(G + q * (S >> R))];
+        for (int q = 0; q < (1 << R); ++q) x[q] = b[q * (S >> R)];
+    } else {
+#pragma unroll
+        for (int q = 0; q < (1 << R); ++q) x[q] = buf[swz(G + q * (S >> R))];
+    }
 }
 template <int R, int S>
 __device__ __forceinline__ void st_str_s(u32 *buf, u32 G, const u32 *x) {
+    if constexpr ((S >> R) % 256 == 0) {
+        u32 *b = buf + swz(G);
 #pragma unroll
-    for (int q = 0; q < (1 << R); ++q) buf[swz(G + q * (S >> R))] = x[q];
+        for (int q = 0; q < (1 << R); ++q) b[q * (S >> R)] = x[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < (1 << R); ++q) buf[swz(G + q * (S >> R))] = x[q];
+    }
 }
 template <int R, int S>
 __device__ __forceinline__ void ld_str_g(const u32 *g, u32 G, u32 *x) {
@@ -182,52 +200,156 @@ __device__ __forceinline__ void row_inv_compute(u32 *x, u32 tid, int t, u32 ib, 
     }
 }
 
-// Large rows: CTA-wide, ping-pong buffers b0/b1 (one barrier per pass).
-// Forward: pass 0 reads the row from global memory; the last pass leaves
-// the leaves in registers (thread tid holds leaves (tid + g*NT) << R .. + 2^R).
-template <class A, int SIGMA, int P>
-__device__ __forceinline__ void lrow_fwd(u32 *x, const u32 *gsrc, u32 *b0, u32 *b1, u32 tid, int t, u32 ib,
-                                         const uint2 *__restrict__ tw, u32 p) {
-    using RP = RowPlan<SIGMA, P>;
-    if constexpr (P == 0) {
-#pragma unroll
-        for (int g = 0; g < RP::NG; ++g) ld_str_g<RP::R, RP::S>(gsrc, tid + g * RP::NT, x + (g << RP::R));
-    } else {
-        const u32 *src = ((P - 1) & 1) ? b1 : b0;
-#pragma unroll
-        for (int g = 0; g < RP::NG; ++g) ld_str_s<RP::R, RP::S>(src, tid + g * RP::NT, x + (g << RP::R));
-    }
-    row_fwd_compute<A, SIGMA, P>(x, tid, t, ib, tw, p);
-    if constexpr (P < RP::NP - 1) {
-        u32 *dst = (P & 1) ? b1 : b0;
-#pragma unroll
-        for (int g = 0; g < RP::NG; ++g) st_con_s<RP::R>(dst, tid + g * RP::NT, x + (g << RP::R));
-        __syncthreads();
-        lrow_fwd<A, SIGMA, P + 1>(x, gsrc, b0, b1, tid, t, ib, tw, p);
+// ------------------------------------------------------ staged large rows
+// Row stage with everything staged in shared memory by cp.async: both rows
+// (natural order, swz layout) and the row's twiddles.  The 2^u twiddles of
+// sub-level u sit at entries [2^u, 2^(u+1)) in node order (entry 0 unused),
+// so a group's 2^d twiddles of one level are contiguous and are read with
+// 16-byte loads (optimal shared-memory wavefronts for the bytes moved).
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    const u32 sa = (u32)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc) {
+    const u32 sa = (u32)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
+    const u32 sa = (u32)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    cp_async_commit();
+    cp_async_wait<0>();
+}
+
+// Copies a row of S words (global, natural order) into buf (swz layout).
+template <int S>
+__device__ __forceinline__ void stage_row(u32 *buf, const u32 *g) {
+    for (u32 ch = threadIdx.x; ch < S / 4; ch += blockDim.x) cp_async16(buf + swz(4 * ch), g + 4 * ch);
+}
+
+// Copies the S-1 twiddles of row ib's subtree (depth t) from the global
+// table into twb (entries [2^u, 2^(u+1)) for sub-level u).
+template <int SIGMA>
+__device__ __forceinline__ void stage_tw(uint2 *twb, const uint2 *__restrict__ tab, int t, u32 ib) {
+    constexpr u32 S = 1u << SIGMA;
+    if (threadIdx.x == 0) cp_async8(twb + 1, tab + tw_index(t, ib));  // level 0: one entry
+    // levels u >= 1: chunk x (two entries) belongs to level u with x + 1 in [2^(u-1), 2^u)
+    for (u32 x = threadIdx.x; x < S / 2 - 1; x += blockDim.x) {
+        const int u = 32 - __clz(x + 1);
+        const u32 q = x + 1 - (1u << (u - 1));
+        cp_async16(twb + (1u << u) + 2 * q, tab + tw_index(t + u, (ib << u) + 2 * q));
     }
 }
 
-// Inverse, starting from the leaves in registers (P = NP-1) and ending with
-// the row written to global memory in natural order.
+// The 2^D twiddles of nodes (v << D) .. (v << D) + 2^D - 1 of one level.
+template <int D>
+__device__ __forceinline__ void ld_tw_level(uint2 *w, const uint2 *lvl, u32 v) {
+    if constexpr (D == 0) {
+        w[0] = lvl[v];
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(lvl + (v << D));
+#pragma unroll
+        for (int e = 0; e < (1 << (D - 1)); ++e) {
+            const uint4 t = q[e];
+            w[2 * e] = make_uint2(t.x, t.y);
+            w[2 * e + 1] = make_uint2(t.z, t.w);
+        }
+    }
+}
+
+template <class A, int R, int U0, int D>
+__device__ __forceinline__ void grp_fwd_s_lvl(u32 *x, const uint2 *twb, u32 v, u32 p) {
+    if constexpr (D < R) {
+        constexpr int half = 1 << (R - 1 - D);
+        uint2 w[1 << D];
+        ld_tw_level<D>(w, twb + (1u << (U0 + D)), v);
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e)
+#pragma unroll
+            for (int jj = 0; jj < half; ++jj) A::ct(x[e * 2 * half + jj], x[e * 2 * half + jj + half], w[e], p);
+        grp_fwd_s_lvl<A, R, U0, D + 1>(x, twb, v, p);
+    }
+}
+template <class A, int R, int U0, int D>
+__device__ __forceinline__ void grp_inv_s_lvl(u32 *x, const uint2 *twb, u32 v, u32 p) {
+    if constexpr (D >= 0) {
+        constexpr int half = 1 << (R - 1 - D);
+        uint2 w[1 << D];
+        ld_tw_level<D>(w, twb + (1u << (U0 + D)), v);
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e)
+#pragma unroll
+            for (int jj = 0; jj < half; ++jj) A::gs(x[e * 2 * half + jj], x[e * 2 * half + jj + half], w[e], p);
+        grp_inv_s_lvl<A, R, U0, D - 1>(x, twb, v, p);
+    }
+}
+template <class A, int R, int U0>
+__device__ __forceinline__ void grp_fwd_s(u32 *x, const uint2 *twb, u32 v, u32 p) {
+    grp_fwd_s_lvl<A, R, U0, 0>(x, twb, v, p);
+}
+template <class A, int R, int U0>
+__device__ __forceinline__ void grp_inv_s(u32 *x, const uint2 *twb, u32 v, u32 p) {
+    grp_inv_s_lvl<A, R, U0, R - 1>(x, twb, v, p);
+}
+
+// Forward passes of both operands, in place (two barriers per pass); the
+// last pass leaves the leaves in registers.
 template <class A, int SIGMA, int P>
-__device__ __forceinline__ void lrow_inv(u32 *x, u32 *gdst, u32 *b0, u32 *b1, u32 tid, int t, u32 ib,
-                                         const uint2 *__restrict__ itw, u32 p) {
+__device__ __forceinline__ void srow2_fwd(u32 *xa, u32 *xb, u32 *ba, u32 *bb, const uint2 *twb, u32 tid, u32 p) {
+    using RP = RowPlan<SIGMA, P>;
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        ld_str_s<RP::R, RP::S>(ba, tid + g * RP::NT, xa + (g << RP::R));
+        ld_str_s<RP::R, RP::S>(bb, tid + g * RP::NT, xb + (g << RP::R));
+    }
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
+        grp_fwd_s<A, RP::R, RP::U0>(xa + (g << RP::R), twb, v, p);
+        grp_fwd_s<A, RP::R, RP::U0>(xb + (g << RP::R), twb, v, p);
+    }
+    if constexpr (P < RP::NP - 1) {
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) {
+            st_con_s<RP::R>(ba, tid + g * RP::NT, xa + (g << RP::R));
+            st_con_s<RP::R>(bb, tid + g * RP::NT, xb + (g << RP::R));
+        }
+        __syncthreads();
+        srow2_fwd<A, SIGMA, P + 1>(xa, xb, ba, bb, twb, tid, p);
+    }
+}
+
+// Inverse passes from the leaves in registers; the last pass (P = 0) writes
+// the row to global memory in natural order.
+template <class A, int SIGMA, int P>
+__device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const uint2 *twb, u32 tid, u32 p) {
     using RP = RowPlan<SIGMA, P>;
     if constexpr (P < RP::NP - 1) {
-        const u32 *src = ((P + 1) & 1) ? b1 : b0;
 #pragma unroll
-        for (int g = 0; g < RP::NG; ++g) ld_con_s<RP::R>(src, tid + g * RP::NT, x + (g << RP::R));
+        for (int g = 0; g < RP::NG; ++g) ld_con_s<RP::R>(ba, tid + g * RP::NT, x + (g << RP::R));
     }
-    row_inv_compute<A, SIGMA, P>(x, tid, t, ib, itw, p);
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
+        grp_inv_s<A, RP::R, RP::U0>(x + (g << RP::R), twb, v, p);
+    }
     if constexpr (P == 0) {
 #pragma unroll
         for (int g = 0; g < RP::NG; ++g) st_str_g<RP::R, RP::S>(gdst, tid + g * RP::NT, x + (g << RP::R));
     } else {
-        u32 *dst = (P & 1) ? b1 : b0;
-#pragma unroll
-        for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(dst, tid + g * RP::NT, x + (g << RP::R));
         __syncthreads();
-        lrow_inv<A, SIGMA, P - 1>(x, gdst, b0, b1, tid, t, ib, itw, p);
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(ba, tid + g * RP::NT, x + (g << RP::R));
+        __syncthreads();
+        srow2_inv<A, SIGMA, P - 1>(x, ba, gdst, twb, tid, p);
     }
 }
 
@@ -265,140 +387,462 @@ __device__ __forceinline__ void srow_inv(u32 *x, u32 *buf, u32 tid, int t, u32 i
 }
 
 // ------------------------------------------------------ column-stage helpers
-// One pass of R tree levels starting at depth s0 over a tile of C columns.
-// Rows of node v: v*M .. v*M+M-1 (M = T >> s0); group (v, j) holds rows
-// v*M + j + q*J, J = M >> R.  With `from_global`, rows come straight from
-// the operand g (row r, column c0+c is element r*S + c0 + c; zero past z).
-template <class A, int R, int C>
-__device__ __forceinline__ void col_fwd_pass(u32 *sm, const u32 *__restrict__ g, int64_t z, int64_t S, int64_t c0,
-                                             int s0, int T, int zb, int k, bool prune, bool from_global,
-                                             const uint2 *__restrict__ tw, u32 p) {
-    const int M = T >> s0, J = M >> R;
-    const int tasks = (T >> R) * C;
-    u32 copymask = 0;
-    if (prune) {
-#pragma unroll
-        for (int d = 0; d < R; ++d)
-            if (zb <= ((M >> d) >> 1)) copymask |= 1u << d;
-    }
-    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-        const int G = tau / C, c = tau % C;
-        const int v = G / J, j = G % J;
-        if (prune && v * M >= k) continue;
-        const int r0 = v * M + j;
-        u32 x[1 << R];
-        if (from_global) {
-#pragma unroll
-            for (int q = 0; q < (1 << R); ++q) {
-                const int64_t e = (int64_t)(r0 + q * J) * S + c0 + c;
-                x[q] = (e < z) ? g[e] : 0u;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < (1 << R); ++q) x[q] = sm[swz((r0 + q * J) * C + c)];
-        }
-        grp_fwd_cp<A, R>(x, tw, s0, (u32)v, p, copymask);
-#pragma unroll
-        for (int q = 0; q < (1 << R); ++q) sm[swz((r0 + q * J) * C + c)] = x[q];
+// A column tile holds rows r < T of C consecutive columns.  Two layouts:
+//  LAY_SWZ  (one-CTA kernel, C = 512): row r, column c at swz(r*C + c), the
+//           same mapping the row stage's Stockham passes use;
+//  LAY_TILE (three-kernel path, C = 8, 16 or 32): row r, column c at
+//           (r ^ h(r))*C + c with h(r) = fold_b(r >> 1), the XOR of the b-bit
+//           chunks of r >> 1, b = log2(32 / C).  A warp spans 32/C tasks;
+//           in every pass shape those tasks' rows then fall in distinct bank
+//           groups (checked exhaustively for T <= 2048).  h is linear over the
+//           disjoint bit fields of a row index r0 | (q << logJ), so per
+//           element it costs one XOR with a compile-time constant.
+// Passes cover at most 4 tree levels (16 registers per task), split evenly.
+enum { LAY_SWZ = 0, LAY_TILE = 1 };
+enum { IO_SMEM = 0, IO_GLOBAL = 1 };
+
+__device__ __forceinline__ int col_npass(int t) { return (t + 3) / 4; }
+__device__ __forceinline__ int col_pass_R(int t, int npass, int idx) { return t / npass + (idx < t % npass ? 1 : 0); }
+
+// XOR of the b-bit chunks of x (b = 1 or 2); a loop, so a literal x folds.
+__host__ __device__ __forceinline__ constexpr u32 cfold(u32 x, int b) {
+    u32 h = 0;
+    for (int i = 0; i < 32; i += b) h ^= (x >> i) & ((1u << b) - 1u);
+    return h;
+}
+template <int C>
+struct TileSw {
+    static constexpr int b = (C >= 32) ? 0 : (C == 16 ? 1 : 2);
+};
+template <int C>
+__device__ __forceinline__ u32 tile_h(u32 r) {
+    constexpr int b = TileSw<C>::b;
+    if constexpr (b == 0) {
+        return 0u;
+    } else if constexpr (b == 1) {
+        return __popc(r >> 1) & 1u;
+    } else {
+        u32 x = r >> 1;
+        x ^= x >> 16;
+        x ^= x >> 8;
+        x ^= x >> 4;
+        x ^= x >> 2;
+        return x & 3u;
     }
 }
 
-// Forward column stage of one tile: t levels (T = 2^t rows); leaves the
-// tile (rows < k valid) in shared memory.  zb = rows with any nonzero input.
-template <class A, int C>
-__device__ void col_fwd_tile(u32 *sm, const u32 *__restrict__ g, int64_t z, int64_t S, int64_t c0, int T, int t,
-                             int zb, int k, bool prune, const uint2 *__restrict__ tw, u32 p) {
-    if (t == 0) {
+// Address of element q (row r0 + (q << logJ), column c) of a task.  The row
+// swizzle is applied after the (disjoint-bit) sum, as h(r0) ^ h(q << logJ).
+template <int C, int LAY>
+struct ColAddr {
+    u32 base;  // r0 * C + c
+    u32 H0;    // h(r0) * C
+    int mode;  // which compile-time swizzle constant applies to q << logJ
+    int sh;    // logJ + log2(C)
+    __device__ __forceinline__ ColAddr(u32 r0, u32 c, int logJ) {
+        sh = logJ + (31 - __clz(C));
+        base = r0 * C + c;
+        if constexpr (LAY == LAY_TILE) {
+            H0 = tile_h<C>(r0) * C;
+            mode = logJ == 0 ? 0 : (((logJ - 1) & 1) ? 2 : 1);
+        } else {
+            H0 = 0;
+            mode = 0;
+        }
+    }
+    __device__ __forceinline__ u32 at(int q) const {  // q is a literal after unrolling
+        const u32 w = base + ((u32)q << sh);
+        if constexpr (LAY == LAY_SWZ) {
+            return swz(w);
+        } else {
+            constexpr int b = TileSw<C>::b;
+            if constexpr (b == 0) {
+                return w;
+            } else {
+                // h(q << logJ) for logJ = 0, logJ >= 1 with logJ - 1 even, odd
+                const u32 h0 = cfold((u32)q >> 1, b) * C, h1 = cfold((u32)q, b) * C, h2 = cfold((u32)q << 1, b) * C;
+                const u32 hq = mode == 0 ? h0 : (mode == 1 ? h1 : h2);
+                return w ^ H0 ^ hq;
+            }
+        }
+    }
+};
+
+struct ColFwdArgs {
+    u32 *sm;            // tile in shared memory
+    const u32 *g;       // operand (global)
+    u32 *W;             // workspace rows (global), row r column c0+c at r*S + c0 + c
+    int64_t z;          // operand length
+    u32 c0;             // first column of the tile
+    int logS;           // log2 of the row length S
+    int T, t;           // rows, tree levels of the column stage
+    int zb;             // rows holding any nonzero input
+    int k;              // rows needed
+    bool prune;
+    const uint2 *tw;
+    u32 p;
+};
+
+// One forward pass of R levels starting at depth s0.
+template <class A, int R, int C, int LAY, int SRC, int DST>
+__device__ __forceinline__ void colf_pass(const ColFwdArgs &X, int s0) {
+    constexpr int logC = ilog2c(C);
+    const int logM = X.t - s0, logJ = logM - R;
+    const int M = 1 << logM;
+    const int tasks = (X.T >> R) << logC;
+    u32 copymask = 0;
+    if (X.prune) {
+#pragma unroll
+        for (int d = 0; d < R; ++d)
+            if (X.zb <= ((M >> d) >> 1)) copymask |= 1u << d;
+    }
+    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
+        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
+        if (X.prune && (int)(v << logM) >= X.k) continue;
+        const u32 r0 = (v << logM) + j;
+        u32 x[1 << R];
+        if constexpr (SRC == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) {
+                const u32 e = e0 + ((u32)q << sh);
+                x[q] = ((int64_t)e < X.z) ? __ldg(X.g + e) : 0u;
+            }
+        } else {
+            const ColAddr<C, LAY> ad(r0, c, logJ);
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) x[q] = X.sm[ad.at(q)];
+        }
+        grp_fwd_cp<A, R>(x, X.tw, s0, v, X.p, copymask);
+        if constexpr (DST == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q)
+                if ((int)(r0 + ((u32)q << logJ)) < X.k) X.W[e0 + ((u32)q << sh)] = x[q];
+        } else {
+            const ColAddr<C, LAY> ad(r0, c, logJ);
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) X.sm[ad.at(q)] = x[q];
+        }
+    }
+}
+
+template <class A, int C, int LAY, int SRC, int DST>
+__device__ __forceinline__ void colf_pass_r(int R, const ColFwdArgs &X, int s0) {
+    // at most 4 levels: one 16-word register array; an if-chain over sizes
+    // up to 4 keeps it in registers (a 32-word variant next to others spills it)
+    if (R == 4) colf_pass<A, 4, C, LAY, SRC, DST>(X, s0);
+    else if (R == 3) colf_pass<A, 3, C, LAY, SRC, DST>(X, s0);
+    else if (R == 2) colf_pass<A, 2, C, LAY, SRC, DST>(X, s0);
+    else colf_pass<A, 1, C, LAY, SRC, DST>(X, s0);
+}
+
+// Forward column stage of one tile.  The first pass reads the operand from
+// global memory; with `to_global` the last pass writes rows < k to the
+// workspace, otherwise the tile ends in shared memory (followed by a barrier).
+template <class A, int C, int LAY>
+__device__ void colf_tile(const ColFwdArgs &X, bool to_global) {
+    if (X.t == 0) {  // one row: plain copy
         for (int c = threadIdx.x; c < C; c += blockDim.x) {
-            const int64_t e = c0 + c;
-            sm[swz(c)] = (e < z) ? g[e] : 0u;
+            const u32 e = X.c0 + c;
+            const u32 v = ((int64_t)e < X.z) ? __ldg(X.g + e) : 0u;
+            if (to_global) X.W[e] = v;
+            else X.sm[LAY == LAY_SWZ ? swz(c) : (u32)c] = v;
         }
         __syncthreads();
         return;
     }
-    for (int s0 = 0; s0 < t; s0 += 4) {
-        const int R = min(4, t - s0);
-        const bool fg = (s0 == 0);
-        switch (R) {
-            case 4: col_fwd_pass<A, 4, C>(sm, g, z, S, c0, s0, T, zb, k, prune, fg, tw, p); break;
-            case 3: col_fwd_pass<A, 3, C>(sm, g, z, S, c0, s0, T, zb, k, prune, fg, tw, p); break;
-            case 2: col_fwd_pass<A, 2, C>(sm, g, z, S, c0, s0, T, zb, k, prune, fg, tw, p); break;
-            default: col_fwd_pass<A, 1, C>(sm, g, z, S, c0, s0, T, zb, k, prune, fg, tw, p); break;
-        }
+    const int np = col_npass(X.t);
+    int s0 = 0;
+    for (int i = 0; i < np; ++i) {
+        const int R = col_pass_R(X.t, np, i);
+        const bool first = i == 0, last = i == np - 1;
+        if (first && last && to_global) colf_pass_r<A, C, LAY, IO_GLOBAL, IO_GLOBAL>(R, X, s0);
+        else if (first) colf_pass_r<A, C, LAY, IO_GLOBAL, IO_SMEM>(R, X, s0);
+        else if (last && to_global) colf_pass_r<A, C, LAY, IO_SMEM, IO_GLOBAL>(R, X, s0);
+        else colf_pass_r<A, C, LAY, IO_SMEM, IO_SMEM>(R, X, s0);
         __syncthreads();
+        s0 += R;
     }
 }
 
-// Inverse pass of R levels [lev0, lev0+R) inside the subtree rooted at
-// (s_root, i_root) that covers rows [base, base + M_root).
-template <class A, int R, int C>
-__device__ __forceinline__ void col_inv_pass(u32 *sm, int lev0, int s_root, u32 i_root, int base, int Msub,
-                                             int nnodes, const uint2 *__restrict__ itw, u32 p) {
-    const int J = Msub >> R;
-    const int tasks = nnodes * J * C;
+struct ColInvArgs {
+    u32 *sm;
+    const u32 *W;   // workspace rows (global) for a first pass from global memory
+    u32 *out;       // product (global) for a last pass to global memory
+    int64_t n;      // product length
+    u32 c0;
+    int logS;
+    int k;          // rows that hold spectral values / output coefficients
+    const uint2 *itw;
+    u32 p;
+};
+
+// Inverse pass of R levels [lev0, lev0+R) of the subtree rooted at (s_root,
+// i_root) covering rows [base, base + 2^logMroot); nodes at depth lev0 have
+// 2^logMsub rows.
+template <class A, int R, int C, int LAY, int SRC, int DST>
+__device__ __forceinline__ void coli_pass(const ColInvArgs &X, int lev0, int s_root, u32 i_root, int base,
+                                          int logMsub, int logNodes) {
+    constexpr int logC = ilog2c(C);
+    const int logJ = logMsub - R;
+    const int tasks = 1 << (logNodes + logJ + logC);
     for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-        const int G = tau / C, c = tau % C;
-        const int v = G / J, j = G % J;
-        const int r0 = base + v * Msub + j;
+        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
+        const u32 r0 = (u32)base + (v << logMsub) + j;
         u32 x[1 << R];
+        if constexpr (SRC == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
 #pragma unroll
-        for (int q = 0; q < (1 << R); ++q) x[q] = sm[swz((r0 + q * J) * C + c)];
-        grp_inv<A, R>(x, itw, lev0, (i_root << (lev0 - s_root)) + (u32)v, p);
+            for (int q = 0; q < (1 << R); ++q) x[q] = __ldcg(X.W + e0 + ((u32)q << sh));
+        } else {
+            const ColAddr<C, LAY> ad(r0, c, logJ);
 #pragma unroll
-        for (int q = 0; q < (1 << R); ++q) sm[swz((r0 + q * J) * C + c)] = x[q];
+            for (int q = 0; q < (1 << R); ++q) x[q] = X.sm[ad.at(q)];
+        }
+        grp_inv<A, R>(x, X.itw, lev0, (i_root << (lev0 - s_root)) + v, X.p);
+        if constexpr (DST == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) {
+                const u32 e = e0 + ((u32)q << sh);
+                if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[q], X.p);
+            }
+        } else {
+            const ColAddr<C, LAY> ad(r0, c, logJ);
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) X.sm[ad.at(q)] = x[q];
+        }
     }
 }
 
-// Unscaled inverse of the whole subtree (s, i) on rows [base, base+M):
-// returns M times the node's coefficients.  Ends with a barrier.
-template <class A, int C>
-__device__ void col_full_inv(u32 *sm, int s, u32 i, int base, int M, const uint2 *__restrict__ itw, u32 p) {
-    const int lm = 31 - __clz(M);
-    const int nch = (lm + 3) / 4;
-    for (int ch = nch - 1; ch >= 0; --ch) {
-        const int u0 = s + 4 * ch;
-        const int R = min(4, lm - 4 * ch);
-        const int Msub = M >> (4 * ch), nn = 1 << (4 * ch);
-        switch (R) {
-            case 4: col_inv_pass<A, 4, C>(sm, u0, s, i, base, Msub, nn, itw, p); break;
-            case 3: col_inv_pass<A, 3, C>(sm, u0, s, i, base, Msub, nn, itw, p); break;
-            case 2: col_inv_pass<A, 2, C>(sm, u0, s, i, base, Msub, nn, itw, p); break;
-            default: col_inv_pass<A, 1, C>(sm, u0, s, i, base, Msub, nn, itw, p); break;
-        }
+template <class A, int C, int LAY, int SRC, int DST>
+__device__ __forceinline__ void coli_pass_r(int R, const ColInvArgs &X, int lev0, int s_root, u32 i_root, int base,
+                                            int logMsub, int logNodes) {
+    if (R == 4) coli_pass<A, 4, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else if (R == 3) coli_pass<A, 3, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else if (R == 2) coli_pass<A, 2, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else coli_pass<A, 1, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+}
+
+// Unscaled inverse of the subtree (s, i) on rows [base, base + 2^lm): M times
+// its coefficients.  Passes run from the deepest levels up.  from_g: the
+// first pass reads the workspace; to_g: the last pass writes the product.
+// Ends with a barrier.
+template <class A, int C, int LAY>
+__device__ void coli_full(const ColInvArgs &X, int s, u32 i, int base, int lm, bool from_g, bool to_g) {
+    if (lm == 0) return;
+    const int np = col_npass(lm);
+    // chunk ch covers relative depths [d0(ch), d0(ch) + R(ch)); executed from ch = np-1 down to 0
+    for (int ch = np - 1; ch >= 0; --ch) {
+        int d0 = 0;
+        for (int q = 0; q < ch; ++q) d0 += col_pass_R(lm, np, q);
+        const int R = col_pass_R(lm, np, ch);
+        const bool first = ch == np - 1, last = ch == 0;
+        const int lev0 = s + d0, logMsub = lm - d0, logNodes = d0;
+        if (first && from_g && last && to_g)
+            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_GLOBAL>(R, X, lev0, s, i, base, logMsub, logNodes);
+        else if (first && from_g)
+            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_SMEM>(R, X, lev0, s, i, base, logMsub, logNodes);
+        else if (last && to_g)
+            coli_pass_r<A, C, LAY, IO_SMEM, IO_GLOBAL>(R, X, lev0, s, i, base, logMsub, logNodes);
+        else
+            coli_pass_r<A, C, LAY, IO_SMEM, IO_SMEM>(R, X, lev0, s, i, base, logMsub, logNodes);
         __syncthreads();
     }
 }
 
-// The truncated inverse (ITFT) of a tile from its step list.  On entry rows
-// [0, k) hold spectral values (all at one common scale) and rows [k, T) are
-// zero; on exit rows [0, k) hold the coefficients at that scale (or, when the
-// list is a single top-level ST_FULL, T times it).  Values in [0, B).
-template <class A, int C>
-__device__ void col_itft_steps(u32 *sm, const ItftStep *__restrict__ steps, int nsteps,
-                               const uint2 *__restrict__ itw, u32 p) {
+// ------------------------------------------- compile-time column passes
+// The same passes with the column depth TL (and so every pass shape, shift
+// and twiddle offset) known at compile time; used by the one-product
+// kernels.  An element address is one XOR with a constant and an immediate
+// offset: (r0*C + c) ^ h(r0)*C ^ h(q<<logJ)*C + (q << (logJ + log2 C)), the
+// XOR and the add commuting when logJ >= b (disjoint bits).
+template <int C, int LOGJ, int Q>
+struct CtAddr {
+    static constexpr int b = TileSw<C>::b;
+    static constexpr int mode = LOGJ == 0 ? 0 : (((LOGJ - 1) & 1) ? 2 : 1);
+    static constexpr u32 hq =
+        b == 0 ? 0u : (mode == 0 ? cfold((u32)Q >> 1, b) : (mode == 1 ? cfold((u32)Q, b) : cfold((u32)Q << 1, b))) * C;
+    static constexpr u32 off = (u32)Q << (LOGJ + ilog2c(C));
+    // rc = r0*C + c, H0 = h(r0)*C
+    static __device__ __forceinline__ u32 at(u32 rc, u32 H0) {
+        if constexpr (b == 0) return rc + off;
+        else if constexpr (LOGJ >= b) return ((rc ^ H0) ^ hq) + off;
+        else return (rc + off) ^ H0 ^ hq;
+    }
+};
+
+template <int C, int LOGJ, int R, int Q = 0>
+__device__ __forceinline__ void ct_load(u32 *x, const u32 *sm, u32 rc, u32 H0) {
+    if constexpr (Q < (1 << R)) {
+        x[Q] = sm[CtAddr<C, LOGJ, Q>::at(rc, H0)];
+        ct_load<C, LOGJ, R, Q + 1>(x, sm, rc, H0);
+    }
+}
+template <int C, int LOGJ, int R, int Q = 0>
+__device__ __forceinline__ void ct_store(const u32 *x, u32 *sm, u32 rc, u32 H0) {
+    if constexpr (Q < (1 << R)) {
+        sm[CtAddr<C, LOGJ, Q>::at(rc, H0)] = x[Q];
+        ct_store<C, LOGJ, R, Q + 1>(x, sm, rc, H0);
+    }
+}
+
+// Forward pass of R levels at depth S0 of a TL-level column stage.
+template <class A, int R, int C, int TL, int S0, int DST>
+__device__ __forceinline__ void colf_pass_ct(const ColFwdArgs &X, u32 copymask) {
+    constexpr int logC = ilog2c(C), logM = TL - S0, logJ = logM - R;
+    constexpr int tasks = (1 << (TL - R)) << logC;
+    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
+        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
+        if (X.prune && (int)(v << logM) >= X.k) continue;
+        const u32 r0 = (v << logM) | j;
+        const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
+        u32 x[1 << R];
+        ct_load<C, logJ, R>(x, X.sm, rc, H0);
+        grp_fwd_cp<A, R>(x, X.tw, S0, v, X.p, copymask >> S0);
+        if constexpr (DST == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q)
+                if ((int)(r0 + ((u32)q << logJ)) < X.k) X.W[e0 + ((u32)q << sh)] = x[q];
+        } else {
+            ct_store<C, logJ, R>(x, X.sm, rc, H0);
+        }
+    }
+}
+
+template <int TL, int I>
+struct ColSplit {  // pass I of an even split of TL levels into passes of <= 4
+    static constexpr int np = (TL + 3) / 4;
+    static constexpr int R = TL / np + (I < TL % np ? 1 : 0);
+    static constexpr int S0 = I == 0 ? 0 : ColSplit<TL, I - 1>::S0 + ColSplit<TL, I - 1>::R;
+};
+template <int TL>
+struct ColSplit<TL, -1> {
+    static constexpr int R = 0, S0 = 0;
+};
+
+template <class A, int C, int TL, int I>
+__device__ __forceinline__ void colf_passes_ct(const ColFwdArgs &X, u32 copymask) {
+    using P = ColSplit<TL, I>;
+    if constexpr (I < P::np) {
+        if constexpr (I == P::np - 1) {
+            colf_pass_ct<A, P::R, C, TL, P::S0, IO_GLOBAL>(X, copymask);
+        } else {
+            colf_pass_ct<A, P::R, C, TL, P::S0, IO_SMEM>(X, copymask);
+        }
+        __syncthreads();
+        colf_passes_ct<A, C, TL, I + 1>(X, copymask);
+    }
+}
+
+// Whole forward column stage of a loaded tile (TL >= 1 levels); the last pass
+// writes rows < k of the workspace.  Ends with a barrier.
+template <class A, int C, int TL>
+__device__ __forceinline__ void colf_tile_ct(const ColFwdArgs &X) {
+    u32 copymask = 0;  // bit s: every upper input at depth s is zero
+    if (X.prune) {
+#pragma unroll
+        for (int s = 0; s < TL; ++s)
+            if (X.zb <= ((X.T >> s) >> 1)) copymask |= 1u << s;
+    }
+    colf_passes_ct<A, C, TL, 0>(X, copymask);
+}
+
+// Inverse pass of R levels at depth S0 of a full TL-level column inverse.
+template <class A, int R, int C, int TL, int S0, int DST>
+__device__ __forceinline__ void coli_pass_ct(const ColInvArgs &X) {
+    constexpr int logC = ilog2c(C), logM = TL - S0, logJ = logM - R;
+    constexpr int tasks = (1 << (TL - R)) << logC;
+    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
+        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
+        const u32 r0 = (v << logM) | j;
+        const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
+        u32 x[1 << R];
+        ct_load<C, logJ, R>(x, X.sm, rc, H0);
+        grp_inv<A, R>(x, X.itw, S0, v, X.p);
+        if constexpr (DST == IO_GLOBAL) {
+            const u32 e0 = (r0 << X.logS) + X.c0 + c;
+            const int sh = logJ + X.logS;
+#pragma unroll
+            for (int q = 0; q < (1 << R); ++q) {
+                const u32 e = e0 + ((u32)q << sh);
+                if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[q], X.p);
+            }
+        } else {
+            ct_store<C, logJ, R>(x, X.sm, rc, H0);
+        }
+    }
+}
+
+template <class A, int C, int TL, int I>
+__device__ __forceinline__ void coli_passes_ct(const ColInvArgs &X) {
+    using P = ColSplit<TL, I>;
+    if constexpr (I >= 0) {
+        if constexpr (I == 0) {
+            coli_pass_ct<A, P::R, C, TL, P::S0, IO_GLOBAL>(X);
+        } else {
+            coli_pass_ct<A, P::R, C, TL, P::S0, IO_SMEM>(X);
+        }
+        __syncthreads();
+        coli_passes_ct<A, C, TL, I - 1>(X);
+    }
+}
+
+// Full unscaled inverse of a loaded TL-level tile, deepest pass first; the
+// top pass writes the product.  Ends with a barrier.
+template <class A, int C, int TL>
+__device__ __forceinline__ void coli_full_ct(const ColInvArgs &X) {
+    coli_passes_ct<A, C, TL, ColSplit<TL, 0>::np - 1>(X);
+}
+
+template <int C, int LAY>
+__device__ __forceinline__ u32 col_elem_addr(u32 r, u32 c) {
+    if constexpr (LAY == LAY_SWZ) return swz(r * C + c);
+    else return (r * C + c) ^ (tile_h<C>(r) * C);
+}
+
+// The truncated inverse (ITFT) of a tile in shared memory from its step list.
+// On entry rows [0, k) hold spectral values (one common scale); rows >= k are
+// never read before written.  On exit rows [0, k) hold the coefficients at
+// that scale (a lone top-level ST_FULL gives T times it).  Values in [0, B).
+template <class A, int C, int LAY>
+__device__ void coli_steps(const ColInvArgs &X, const ItftStep *__restrict__ steps, int nsteps) {
+    constexpr int logC = ilog2c(C);
+    const u32 p = X.p;
     for (int si = 0; si < nsteps; ++si) {
         const ItftStep st = steps[si];
         if (st.kind == ST_FULL) {
-            col_full_inv<A, C>(sm, st.s, st.i, st.base, st.h, itw, p);
+            coli_full<A, C, LAY>(X, st.s, st.i, st.base, 31 - __clz(st.h), false, false);
             continue;
         }
         const bool upper = (st.kind == ST_PRE_RIGHT || st.kind == ST_PRE_LEFT);
         const int lo = upper ? st.m : 0, hi = upper ? st.h : st.m;
-        const int tasks = (hi - lo) * C;
+        const int tasks = (hi - lo) << logC;
         for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-            const int j = lo + tau / C, c = tau % C;
-            u32 *X0 = sm + swz((st.base + j) * C + c);
-            u32 *X1 = sm + swz((st.base + j + st.h) * C + c);
+            const u32 j = (u32)lo + ((u32)tau >> logC), c = (u32)tau & (C - 1);
+            u32 *X0 = X.sm + col_elem_addr<C, LAY>((u32)st.base + j, c);
+            u32 *X1 = X.sm + col_elem_addr<C, LAY>((u32)(st.base + st.h) + j, c);
             const u32 x0 = A::to_canon(*X0, p), x1 = A::to_canon(*X1, p);
             switch (st.kind) {
                 case ST_PRE_RIGHT: {
-                    const u32 lo_ = mul_c(x0, st.hinv, p);
+                    const u32 l = mul_c(x0, st.hinv, p);
                     if (st.zero) {
-                        *X0 = lo_;
-                        *X1 = lo_;
+                        *X0 = l;
+                        *X1 = l;
                     } else {
                         const u32 rc = mul_c(x1, st.r, p);
-                        const u32 cj = sub_c(lo_, rc, p);
+                        const u32 cj = sub_c(l, rc, p);
                         *X0 = cj;
                         *X1 = sub_c(cj, rc, p);
                     }

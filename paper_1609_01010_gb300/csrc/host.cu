@@ -310,18 +310,17 @@ Schedule default_schedule(int l) {
     else if (l <= 20) s.sigma = 11;
     else if (l <= 22) s.sigma = 12;
     else s.sigma = 13;
-    const int t = l - s.sigma;
-    s.C = t >= 9 ? 16 : 32;
-    if (t >= 11) s.C = 16;
+    s.C = 8;
     return s;
 }
 
+// Column tiles are double-buffered: 2 * T * C words must fit 128 KB.
 bool schedule_valid(int l, Schedule s) {
     if (s.sigma < 9 || s.sigma > 13 || s.sigma > l) return false;
-    if (s.C != 8 && s.C != 16 && s.C != 32) return false;
+    if (s.C != 8 && s.C != 32 && s.C != 128) return false;
     const int t = l - s.sigma;
     if (t > 11) return false;
-    if (((int64_t)1 << t) * s.C * 4 > 160 * 1024) return false;
+    if (((int64_t)2 << t) * s.C * 4 > 128 * 1024) return false;
     if (((int64_t)1 << s.sigma) < s.C) return false;
     return true;
 }

@@ -71,6 +71,10 @@ constexpr int SMALL_MAX_LOG_L = SMALL_LOG_S + SMALL_MAX_LOG_T;
 // column tiles of C words handled by one CTA each, T <= 1024 rows.
 constexpr int LARGE_MAX_LOG_T = 10;
 
+// Shared memory of one row of the row stage: both operands' rows (2 S words)
+// and the row's twiddles (S entries of 8 bytes, entry 0 unused).
+inline size_t row_smem_bytes(int sigma) { return ((size_t)2 << sigma) * 4 + ((size_t)1 << sigma) * 8; }
+
 struct Schedule {
     int sigma;  // row-block log size
     int C;      // column tile width
@@ -85,6 +89,10 @@ inline cudaError_t ensure_smem(K kern, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return ensure_smem_ptr((const void *)kern, bytes);
 }
+
+// Grid of a persistent kernel: all CTAs that fit on the device at once, at
+// most `items`.
+cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int items, int *grid);
 
 // ------------------------------------------------------------ launchers
 // Kernels are launched only through these (defined in k_small.cu /

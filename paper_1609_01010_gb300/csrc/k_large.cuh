@@ -16,49 +16,103 @@
 namespace pm {
 
 constexpr int COL_THREADS = 256;
-constexpr size_t COL_SMEM_MAX = 160 * 1024;  // T * C * 4 bytes (schedule_valid's bound)
+constexpr size_t COL_SMEM_MAX = 128 * 1024;  // 2 * T * C * 4 bytes (schedule_valid's bound)
 
-template <class A, int C>
-__global__ void __launch_bounds__(COL_THREADS) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
-    colf_body<A, C>(d, blockIdx.x, blockIdx.y, m, tw);
+// Persistent column kernels: each CTA walks items blockIdx.x, +gridDim.x, ...
+// and double-buffers them: the cp.async copies of the next item are in
+// flight while the current one computes.  TL = column depth (compile time).
+template <class A, int C, int TL>
+__global__ void __launch_bounds__(COL_THREADS, 3) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
+    u32 *smem = dyn_smem();
+    const u32 words = (u32)C << TL;
+    const int items = 2 * (int)(d.g.S / C);  // (tile, operand) pairs
+    int it = blockIdx.x;
+    if (it < items) colf_load<C>(d, it >> 1, it & 1, smem);
+    cp_async_commit();
+    for (int kb = 0; it < items; it += gridDim.x, kb ^= 1) {
+        const int nx = it + gridDim.x;
+        if (nx < items) colf_load<C>(d, nx >> 1, nx & 1, smem + (kb ^ 1) * words);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        colf_compute_ct<A, C, TL>(d, it >> 1, it & 1, smem + kb * words, m, tw);
+    }
 }
 
 template <class A, int SIGMA>
-__global__ void __launch_bounds__((1 << SIGMA) / 16) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
+__global__ void __launch_bounds__((1 << SIGMA) / 16, (SIGMA >= 13 ? 1 : (SIGMA == 12 ? 3 : 2))) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
     row_body<A, SIGMA>(d, blockIdx.x, m, tw);
 }
 
-template <class A, int C>
-__global__ void __launch_bounds__(COL_THREADS) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
-    coli_body<A, C>(d, blockIdx.x, m, tw);
+template <class A, int C, int TL>
+__global__ void __launch_bounds__(COL_THREADS, 3) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
+    u32 *smem = dyn_smem();
+    const u32 words = (u32)C << TL;
+    const int items = (int)(d.g.S / C);
+    int it = blockIdx.x;
+    if (it < items) coli_load<C>(d, it, smem);
+    cp_async_commit();
+    for (int kb = 0; it < items; it += gridDim.x, kb ^= 1) {
+        const int nx = it + gridDim.x;
+        if (nx < items) coli_load<C>(d, nx, smem + (kb ^ 1) * words);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        coli_compute_ct<A, C, TL>(d, it, smem + kb * words, m, tw);
+    }
 }
 
 // ------------------------------------------------------------ launchers
-
-template <class A, int C>
-static cudaError_t launch_cols(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
-    const size_t smem = (size_t)d.g.T * C * sizeof(u32);
-    cudaError_t e = ensure_smem(k_col_fwd<A, C>, COL_SMEM_MAX);
+template <class A, int C, int TL>
+static cudaError_t launch_colf_c(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
+    const size_t smem = (size_t)2 * ((size_t)C << TL) * sizeof(u32);
+    cudaError_t e = ensure_smem(k_col_fwd<A, C, TL>, COL_SMEM_MAX);
     if (e != cudaSuccess) return e;
-    e = ensure_smem(k_col_itft<A, C>, COL_SMEM_MAX);
+    int grid = 0;
+    e = persistent_grid((const void *)k_col_fwd<A, C, TL>, COL_THREADS, smem, 2 * (int)(d.g.S / C), &grid);
     if (e != cudaSuccess) return e;
-    const int tiles = (int)(d.g.S / C);
-    k_col_fwd<A, C><<<dim3(tiles, 2), COL_THREADS, smem, st>>>(d, m, tw);
+    k_col_fwd<A, C, TL><<<grid, COL_THREADS, smem, st>>>(d, m, tw);
     return cudaGetLastError();
 }
 
-template <class A, int C>
-static cudaError_t launch_cols_inv(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
-    const size_t smem = (size_t)d.g.T * C * sizeof(u32);
-    const int tiles = (int)(d.g.S / C);
-    k_col_itft<A, C><<<tiles, COL_THREADS, smem, st>>>(d, m, tw);
+template <class A, int C, int TL>
+static cudaError_t launch_coli_c(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
+    const size_t smem = (size_t)2 * ((size_t)C << TL) * sizeof(u32);
+    cudaError_t e = ensure_smem(k_col_itft<A, C, TL>, COL_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    int grid = 0;
+    e = persistent_grid((const void *)k_col_itft<A, C, TL>, COL_THREADS, smem, (int)(d.g.S / C), &grid);
+    if (e != cudaSuccess) return e;
+    k_col_itft<A, C, TL><<<grid, COL_THREADS, smem, st>>>(d, m, tw);
     return cudaGetLastError();
+}
+
+// t in 1..11 (schedule_valid); C in {8, 32, 128}.
+template <class A, int C, bool FWD>
+static cudaError_t launch_col_t(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
+#define PM_COL_CASE(TLV) \
+    case TLV: return FWD ? launch_colf_c<A, C, TLV>(d, m, tw, st) : launch_coli_c<A, C, TLV>(d, m, tw, st);
+    switch (d.g.t) {
+        PM_COL_CASE(1)
+        PM_COL_CASE(2)
+        PM_COL_CASE(3)
+        PM_COL_CASE(4)
+        PM_COL_CASE(5)
+        PM_COL_CASE(6)
+        PM_COL_CASE(7)
+        PM_COL_CASE(8)
+        PM_COL_CASE(9)
+        PM_COL_CASE(10)
+        PM_COL_CASE(11)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PM_COL_CASE
 }
 
 template <class A, int SIGMA>
 static cudaError_t launch_rows(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
     constexpr int S = 1 << SIGMA;
-    const size_t smem = (size_t)4 * S * sizeof(u32);
+    const size_t smem = row_smem_bytes(SIGMA);
     cudaError_t e = ensure_smem(k_row_fused<A, SIGMA>, smem);
     if (e != cudaSuccess) return e;
     k_row_fused<A, SIGMA><<<(int)d.g.k, S / 16, smem, st>>>(d, m, tw);
@@ -66,35 +120,15 @@ static cudaError_t launch_rows(const LargeDesc &d, ModParams m, TwTables tw, cud
 }
 
 template <class A>
-static cudaError_t launch_large_t(const LargeDesc &d, Schedule sch, ModParams m, TwTables tw, cudaStream_t st,
-                                  cudaEvent_t *ev) {
-    cudaError_t e;
-    if (ev) cudaEventRecord(ev[0], st);
-    switch (sch.C) {
-        case 8: e = launch_cols<A, 8>(d, m, tw, st); break;
-        case 16: e = launch_cols<A, 16>(d, m, tw, st); break;
-        case 32: e = launch_cols<A, 32>(d, m, tw, st); break;
-        default: return cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[1], st);
+static cudaError_t launch_row(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
     switch (d.g.sigma) {
-        case 9: e = launch_rows<A, 9>(d, m, tw, st); break;
-        case 10: e = launch_rows<A, 10>(d, m, tw, st); break;
-        case 11: e = launch_rows<A, 11>(d, m, tw, st); break;
-        case 12: e = launch_rows<A, 12>(d, m, tw, st); break;
-        case 13: e = launch_rows<A, 13>(d, m, tw, st); break;
+        case 9: return launch_rows<A, 9>(d, m, tw, st);
+        case 10: return launch_rows<A, 10>(d, m, tw, st);
+        case 11: return launch_rows<A, 11>(d, m, tw, st);
+        case 12: return launch_rows<A, 12>(d, m, tw, st);
+        case 13: return launch_rows<A, 13>(d, m, tw, st);
         default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[2], st);
-    switch (sch.C) {
-        case 8: e = launch_cols_inv<A, 8>(d, m, tw, st); break;
-        case 16: e = launch_cols_inv<A, 16>(d, m, tw, st); break;
-        default: e = launch_cols_inv<A, 32>(d, m, tw, st); break;
-    }
-    if (ev) cudaEventRecord(ev[3], st);
-    return e;
 }
 
 }  // namespace pm
