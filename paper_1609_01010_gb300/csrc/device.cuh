@@ -81,6 +81,55 @@ __device__ __forceinline__ void grp_fwd_cp(u32 *x, const uint2 *__restrict__ tw,
     }
 }
 
+// Two columns at once (x, y), sharing the twiddle loads.
+template <class A, int R>
+__device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *__restrict__ tw, int lev0, u32 node0, u32 p,
+                                            u32 copymask) {
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+        const int half = 1 << (R - 1 - d);
+        if ((copymask >> d) & 1u) {
+#pragma unroll
+            for (int e = 0; e < (1 << d); ++e)
+#pragma unroll
+                for (int jj = 0; jj < half; ++jj) {
+                    const int lo = e * 2 * half + jj;
+                    x[lo + half] = x[lo];
+                    y[lo + half] = y[lo];
+                }
+        } else {
+#pragma unroll
+            for (int e = 0; e < (1 << d); ++e) {
+                const uint2 w = __ldg(tw + tw_index(lev0 + d, (node0 << d) + e));
+#pragma unroll
+                for (int jj = 0; jj < half; ++jj) {
+                    const int lo = e * 2 * half + jj;
+                    A::ct(x[lo], x[lo + half], w, p);
+                    A::ct(y[lo], y[lo + half], w, p);
+                }
+            }
+        }
+    }
+}
+
+template <class A, int R>
+__device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
+#pragma unroll
+    for (int d = R - 1; d >= 0; --d) {
+        const int half = 1 << (R - 1 - d);
+#pragma unroll
+        for (int e = 0; e < (1 << d); ++e) {
+            const uint2 w = __ldg(itw + tw_index(lev0 + d, (node0 << d) + e));
+#pragma unroll
+            for (int jj = 0; jj < half; ++jj) {
+                const int lo = e * 2 * half + jj;
+                A::gs(x[lo], x[lo + half], w, p);
+                A::gs(y[lo], y[lo + half], w, p);
+            }
+        }
+    }
+}
+
 template <class A, int R>
 __device__ __forceinline__ void grp_inv(u32 *x, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
 #pragma unroll
@@ -277,6 +326,23 @@ __device__ __forceinline__ void grp_fwd_s_lvl(u32 *x, const uint2 *twb, u32 v, u
         grp_fwd_s_lvl<A, R, U0, D + 1>(x, twb, v, p);
     }
 }
+// Both operands of a row with one twiddle load per node.
+template <class A, int R, int U0, int D>
+__device__ __forceinline__ void grp_fwd_s2_lvl(u32 *x, u32 *y, const uint2 *twb, u32 v, u32 p) {
+    if constexpr (D < R) {
+        constexpr int half = 1 << (R - 1 - D);
+        uint2 w[1 << D];
+        ld_tw_level<D>(w, twb + (1u << (U0 + D)), v);
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e)
+#pragma unroll
+            for (int jj = 0; jj < half; ++jj) {
+                A::ct(x[e * 2 * half + jj], x[e * 2 * half + jj + half], w[e], p);
+                A::ct(y[e * 2 * half + jj], y[e * 2 * half + jj + half], w[e], p);
+            }
+        grp_fwd_s2_lvl<A, R, U0, D + 1>(x, y, twb, v, p);
+    }
+}
 template <class A, int R, int U0, int D>
 __device__ __forceinline__ void grp_inv_s_lvl(u32 *x, const uint2 *twb, u32 v, u32 p) {
     if constexpr (D >= 0) {
@@ -312,8 +378,7 @@ __device__ __forceinline__ void srow2_fwd(u32 *xa, u32 *xb, u32 *ba, u32 *bb, co
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
-        grp_fwd_s<A, RP::R, RP::U0>(xa + (g << RP::R), twb, v, p);
-        grp_fwd_s<A, RP::R, RP::U0>(xb + (g << RP::R), twb, v, p);
+        grp_fwd_s2_lvl<A, RP::R, RP::U0, 0>(xa + (g << RP::R), xb + (g << RP::R), twb, v, p);
     }
     if constexpr (P < RP::NP - 1) {
         __syncthreads();
@@ -679,43 +744,48 @@ struct CtAddr {
     }
 };
 
+// Two adjacent columns (c even) per task: one 64-bit access per row.
 template <int C, int LOGJ, int R, int Q = 0>
-__device__ __forceinline__ void ct_load(u32 *x, const u32 *sm, u32 rc, u32 H0) {
+__device__ __forceinline__ void ct_load2(u32 *x, u32 *y, const u32 *sm, u32 rc, u32 H0) {
     if constexpr (Q < (1 << R)) {
-        x[Q] = sm[CtAddr<C, LOGJ, Q>::at(rc, H0)];
-        ct_load<C, LOGJ, R, Q + 1>(x, sm, rc, H0);
+        const uint2 v = *reinterpret_cast<const uint2 *>(sm + CtAddr<C, LOGJ, Q>::at(rc, H0));
+        x[Q] = v.x;
+        y[Q] = v.y;
+        ct_load2<C, LOGJ, R, Q + 1>(x, y, sm, rc, H0);
     }
 }
 template <int C, int LOGJ, int R, int Q = 0>
-__device__ __forceinline__ void ct_store(const u32 *x, u32 *sm, u32 rc, u32 H0) {
+__device__ __forceinline__ void ct_store2(const u32 *x, const u32 *y, u32 *sm, u32 rc, u32 H0) {
     if constexpr (Q < (1 << R)) {
-        sm[CtAddr<C, LOGJ, Q>::at(rc, H0)] = x[Q];
-        ct_store<C, LOGJ, R, Q + 1>(x, sm, rc, H0);
+        *reinterpret_cast<uint2 *>(sm + CtAddr<C, LOGJ, Q>::at(rc, H0)) = make_uint2(x[Q], y[Q]);
+        ct_store2<C, LOGJ, R, Q + 1>(x, y, sm, rc, H0);
     }
 }
 
-// Forward pass of R levels at depth S0 of a TL-level column stage.
+// Forward pass of R levels at depth S0 of a TL-level column stage.  A task is
+// one group of 2^R rows in two adjacent columns.
 template <class A, int R, int C, int TL, int S0, int DST>
 __device__ __forceinline__ void colf_pass_ct(const ColFwdArgs &X, u32 copymask) {
-    constexpr int logC = ilog2c(C), logM = TL - S0, logJ = logM - R;
-    constexpr int tasks = (1 << (TL - R)) << logC;
+    constexpr int logC2 = ilog2c(C) - 1, logM = TL - S0, logJ = logM - R;
+    constexpr int tasks = (1 << (TL - R)) << logC2;
     for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 G = (u32)tau >> logC2, c = ((u32)tau & ((C >> 1) - 1)) << 1;
         const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
         if (X.prune && (int)(v << logM) >= X.k) continue;
         const u32 r0 = (v << logM) | j;
         const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
-        u32 x[1 << R];
-        ct_load<C, logJ, R>(x, X.sm, rc, H0);
-        grp_fwd_cp<A, R>(x, X.tw, S0, v, X.p, copymask >> S0);
+        u32 x[1 << R], y[1 << R];
+        ct_load2<C, logJ, R>(x, y, X.sm, rc, H0);
+        grp_fwd_cp2<A, R>(x, y, X.tw, S0, v, X.p, copymask >> S0);
         if constexpr (DST == IO_GLOBAL) {
             const u32 e0 = (r0 << X.logS) + X.c0 + c;
             const int sh = logJ + X.logS;
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q)
-                if ((int)(r0 + ((u32)q << logJ)) < X.k) X.W[e0 + ((u32)q << sh)] = x[q];
+                if ((int)(r0 + ((u32)q << logJ)) < X.k)
+                    *reinterpret_cast<uint2 *>(X.W + e0 + ((u32)q << sh)) = make_uint2(x[q], y[q]);
         } else {
-            ct_store<C, logJ, R>(x, X.sm, rc, H0);
+            ct_store2<C, logJ, R>(x, y, X.sm, rc, H0);
         }
     }
 }
@@ -758,19 +828,20 @@ __device__ __forceinline__ void colf_tile_ct(const ColFwdArgs &X) {
     colf_passes_ct<A, C, TL, 0>(X, copymask);
 }
 
-// Inverse pass of R levels at depth S0 of a full TL-level column inverse.
+// Inverse pass of R levels at depth S0 of a full TL-level column inverse
+// (two adjacent columns per task).
 template <class A, int R, int C, int TL, int S0, int DST>
 __device__ __forceinline__ void coli_pass_ct(const ColInvArgs &X) {
-    constexpr int logC = ilog2c(C), logM = TL - S0, logJ = logM - R;
-    constexpr int tasks = (1 << (TL - R)) << logC;
+    constexpr int logC2 = ilog2c(C) - 1, logM = TL - S0, logJ = logM - R;
+    constexpr int tasks = (1 << (TL - R)) << logC2;
     for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-        const u32 G = (u32)tau >> logC, c = (u32)tau & (C - 1);
+        const u32 G = (u32)tau >> logC2, c = ((u32)tau & ((C >> 1) - 1)) << 1;
         const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
         const u32 r0 = (v << logM) | j;
         const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
-        u32 x[1 << R];
-        ct_load<C, logJ, R>(x, X.sm, rc, H0);
-        grp_inv<A, R>(x, X.itw, S0, v, X.p);
+        u32 x[1 << R], y[1 << R];
+        ct_load2<C, logJ, R>(x, y, X.sm, rc, H0);
+        grp_inv2<A, R>(x, y, X.itw, S0, v, X.p);
         if constexpr (DST == IO_GLOBAL) {
             const u32 e0 = (r0 << X.logS) + X.c0 + c;
             const int sh = logJ + X.logS;
@@ -778,9 +849,10 @@ __device__ __forceinline__ void coli_pass_ct(const ColInvArgs &X) {
             for (int q = 0; q < (1 << R); ++q) {
                 const u32 e = e0 + ((u32)q << sh);
                 if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[q], X.p);
+                if ((int64_t)e + 1 < X.n) X.out[e + 1] = A::to_canon(y[q], X.p);
             }
         } else {
-            ct_store<C, logJ, R>(x, X.sm, rc, H0);
+            ct_store2<C, logJ, R>(x, y, X.sm, rc, H0);
         }
     }
 }

@@ -15,14 +15,14 @@
 
 namespace pm {
 
-constexpr int COL_THREADS = 256;
+constexpr int COL_THREADS = 128;
 constexpr size_t COL_SMEM_MAX = 128 * 1024;  // 2 * T * C * 4 bytes (schedule_valid's bound)
 
 // Persistent column kernels: each CTA walks items blockIdx.x, +gridDim.x, ...
 // and double-buffers them: the cp.async copies of the next item are in
 // flight while the current one computes.  TL = column depth (compile time).
 template <class A, int C, int TL>
-__global__ void __launch_bounds__(COL_THREADS, 3) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
+__global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     const u32 words = (u32)C << TL;
     const int items = 2 * (int)(d.g.S / C);  // (tile, operand) pairs
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__((1 << SIGMA) / 16, (SIGMA >= 13 ? 1 : (SIGMA =
 }
 
 template <class A, int C, int TL>
-__global__ void __launch_bounds__(COL_THREADS, 3) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
+__global__ void __launch_bounds__(COL_THREADS, 6) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     const u32 words = (u32)C << TL;
     const int items = (int)(d.g.S / C);
