@@ -55,7 +55,6 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
             d.k = sd.k;
             d.steps = sd.steps;
             d.nsteps = sd.nsteps;
-            d.cscale = sd.cscale;
             const size_t sm = (size_t)2 * ((size_t)1 << sd.logT) * (1 << SMALL_LOG_S) * 4;
             smem = std::max(smem, sm);
             small.push_back({d.n, i});
@@ -69,7 +68,6 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
             d.g = ld.g;
             d.steps = ld.steps;
             d.nsteps = ld.nsteps;
-            d.cscale = ld.cscale;
             d.ws_off = ws;
             ws += (uint64_t)2 * ld.g.k * ld.g.S * 4;
             smem = std::max(smem, (size_t)ld.g.T * C * 4);

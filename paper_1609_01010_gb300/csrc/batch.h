@@ -24,7 +24,6 @@ struct BatchDesc {
     int32_t nsteps;
     int32_t large;
     int32_t logT, k;  // small products
-    uint2 cscale;
 };
 
 struct BatchParams {

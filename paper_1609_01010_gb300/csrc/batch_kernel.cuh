@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(BatchParams P) {
                 d.steps = bd.steps;
                 d.nsteps = bd.nsteps;
                 d.prune = 1;
-                d.cscale = bd.cscale;
                 small_dispatch<A>(d, P.m, P.tw);
             } else {
                 LargeDesc d;
@@ -75,7 +74,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(BatchParams P) {
                 d.steps = bd.steps;
                 d.nsteps = bd.nsteps;
                 d.prune = 1;
-                d.cscale = bd.cscale;
                 if (w.kind == IT_COLF) colf_body<A, C>(d, w.idx, w.opnd, P.m, P.tw);
                 else if (w.kind == IT_ROW) row_body_ool<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
                 else coli_body<A, C>(d, w.idx, P.m, P.tw);

@@ -18,6 +18,16 @@ __device__ __forceinline__ u32 *dyn_smem() {
     return pm_dyn_smem;
 }
 
+// The pointwise constant of row r (of k computed rows of 2^sigma words):
+// 2^32 / (2^sigma * h) mod p, where 2^sigma undoes the unscaled row inverse
+// and h is the size of the FULL record of the truncated inverse that covers
+// row r (k's binary expansion splits rows [0, k) into aligned blocks of
+// decreasing powers of two; r lies in the block of size 2^b with b the top
+// bit of r ^ k).  k = T gives the plain 1/L.
+__device__ __forceinline__ uint2 row_scale(const TwTables &tw, int sigma, u32 r, u32 k) {
+    return __ldg(tw.pscale + sigma + (31 - __clz(r ^ k)));
+}
+
 // ---------------------------------------------------------- small product
 // One product with L = T * 512 <= 8192 (see k_small.cu).  Any blockDim that
 // is a multiple of 32; shared memory: 2 * T * 512 words.
@@ -43,12 +53,13 @@ __device__ __forceinline__ void small_body(const SmallDesc &d, ModParams m, TwTa
         u32 xa[16], xb[16];
         srow_fwd<A, SMALL_LOG_S, 0>(xa, sa + w * S, lane, LOGT, (u32)w, tw.fwd, p);
         srow_fwd<A, SMALL_LOG_S, 0>(xb, sb + w * S, lane, LOGT, (u32)w, tw.fwd, p);
+        const uint2 cs = row_scale(tw, SMALL_LOG_S, (u32)w, (u32)d.k);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], d.cscale, m);
+        for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], cs, m);
         srow_inv<A, SMALL_LOG_S, NP - 1>(xa, sa + w * S, lane, LOGT, (u32)w, tw.inv, p);
     }
     __syncthreads();
-    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p};
+    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p, tw.fwd};
     coli_steps<A, S, LAY_SWZ>(Y, d.steps, d.nsteps);
     for (int64_t e = threadIdx.x; e < d.n; e += blockDim.x) d.c[e] = A::to_canon(sa[swz((u32)e)], p);
     __syncthreads();
@@ -178,8 +189,9 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
     __syncthreads();
     u32 xa[16], xb[16];
     srow2_fwd<A, SIGMA, 0>(xa, xb, ba, bb, twb, tid, p);
+    const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], d.cscale, m);
+    for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], cs, m);
     __syncthreads();  // every thread is done with the forward twiddles
     stage_tw<SIGMA>(twb, tw.inv, d.g.t, ib);
     cp_async_wait_all();
@@ -206,14 +218,27 @@ __device__ __forceinline__ void coli_load(const LargeDesc &d, int tile, u32 *buf
     }
 }
 
+// Stores rows [0, k) of a column tile (reduced to [0, p)) to the product,
+// entries below n only.  Ends with a barrier.
+template <class A, int C>
+__device__ __forceinline__ void coli_store(const LargeDesc &d, u32 c0, const u32 *buf, u32 p) {
+    const int k = (int)d.g.k;
+    const int64_t S = d.g.S;
+    for (int tau = threadIdx.x; tau < k * C; tau += blockDim.x) {
+        const u32 r = (u32)tau / C, c = (u32)tau % C;
+        const int64_t e = (int64_t)r * S + c0 + c;
+        if (e < d.n) d.c[e] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(r, c)], p);
+    }
+    __syncthreads();
+}
+
 // ITFT column stage of a tile already in buf, and the store of its part of
 // the first n outputs (reduced to [0, p)).  Ends with a barrier.
 template <class A, int C>
 __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
-    const int64_t S = d.g.S;
     const u32 c0 = (u32)tile * C;
     const int T = (int)d.g.T, k = (int)d.g.k;
-    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p};
+    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p, tw.fwd};
     if (d.g.t == 0) {
         for (int c = threadIdx.x; c < C; c += blockDim.x)
             if ((int64_t)(c0 + c) < d.n) d.c[c0 + c] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(0, c)], m.p);
@@ -225,22 +250,15 @@ __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *
         return;
     }
     coli_steps<A, C, LAY_TILE>(X, d.steps, d.nsteps);
-    for (int tau = threadIdx.x; tau < k * C; tau += blockDim.x) {
-        const u32 r = (u32)tau / C, c = (u32)tau % C;
-        const int64_t e = (int64_t)r * S + c0 + c;
-        if (e < d.n) d.c[e] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(r, c)], m.p);
-    }
-    __syncthreads();
+    coli_store<A, C>(d, c0, buf, m.p);
 }
 
+// Column inverse of a loaded tile with compile-time pass shapes: the full
+// inverse when k = T, the truncated one otherwise (k a multiple of T/8).
 template <class A, int C, int TL>
 __device__ __forceinline__ void coli_compute_ct(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
-    if (d.g.k == d.g.T) {
-        const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p};
-        coli_full_ct<A, C, TL>(X);
-    } else {
-        coli_compute<A, C>(d, tile, buf, m, tw);
-    }
+    const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p, tw.fwd};
+    coli_tile_ct<A, C, TL>(X);
 }
 
 template <class A, int C>

@@ -112,21 +112,28 @@ __device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *__restr
     }
 }
 
-template <class A, int R>
-__device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
+// Node E at relative depth D of an R-level inverse group, then the nodes
+// after it; template recursion keeps every array index a constant.
+template <class A, int R, int D, int E>
+__device__ __forceinline__ void grp_inv2_nodes(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0,
+                                               u32 p) {
+    if constexpr (E < (1 << D)) {
+        constexpr int half = 1 << (R - 1 - D);
+        const uint2 w = __ldg(itw + tw_index(lev0 + D, (node0 << D) + E));
 #pragma unroll
-    for (int d = R - 1; d >= 0; --d) {
-        const int half = 1 << (R - 1 - d);
-#pragma unroll
-        for (int e = 0; e < (1 << d); ++e) {
-            const uint2 w = __ldg(itw + tw_index(lev0 + d, (node0 << d) + e));
-#pragma unroll
-            for (int jj = 0; jj < half; ++jj) {
-                const int lo = e * 2 * half + jj;
-                A::gs(x[lo], x[lo + half], w, p);
-                A::gs(y[lo], y[lo + half], w, p);
-            }
+        for (int jj = 0; jj < half; ++jj) {
+            A::gs(x[E * 2 * half + jj], x[E * 2 * half + jj + half], w, p);
+            A::gs(y[E * 2 * half + jj], y[E * 2 * half + jj + half], w, p);
         }
+        grp_inv2_nodes<A, R, D, E + 1>(x, y, itw, lev0, node0, p);
+    }
+}
+
+template <class A, int R, int D = R - 1>
+__device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
+    if constexpr (D >= 0) {
+        grp_inv2_nodes<A, R, D, 0>(x, y, itw, lev0, node0, p);
+        grp_inv2<A, R, D - 1>(x, y, itw, lev0, node0, p);
     }
 }
 
@@ -644,6 +651,7 @@ struct ColInvArgs {
     int k;          // rows that hold spectral values / output coefficients
     const uint2 *itw;
     u32 p;
+    const uint2 *tw;  // forward table (r of the truncated inverse's records)
 };
 
 // Inverse pass of R levels [lev0, lev0+R) of the subtree rooted at (s_root,
@@ -884,14 +892,21 @@ __device__ __forceinline__ u32 col_elem_addr(u32 r, u32 c) {
     else return (r * C + c) ^ (tile_h<C>(r) * C);
 }
 
+// x / 2 mod p for x in [0, B): (x + p) / 2 when x is odd.  Stays in [0, B).
+__device__ __forceinline__ u32 half_mod(u32 x, u32 p) { return (x + (x & 1u) * p) >> 1; }
+
 // The truncated inverse (ITFT) of a tile in shared memory from its step list.
-// On entry rows [0, k) hold spectral values (one common scale); rows >= k are
-// never read before written.  On exit rows [0, k) hold the coefficients at
-// that scale (a lone top-level ST_FULL gives T times it).  Values in [0, B).
+// On entry rows [0, k) hold spectral values, each already multiplied by
+// 1/h for the size h of the FULL record that inverts it (the row stage
+// folds that factor into its pointwise constant), so every FULL leaves true
+// coefficients and no record needs an h^-1 multiply.  Rows >= k are never
+// read before written.  On exit rows [0, k) hold the coefficients.  Values
+// stay in [0, B) throughout.  Elementwise records handle two adjacent
+// columns per task.
 template <class A, int C, int LAY>
 __device__ void coli_steps(const ColInvArgs &X, const ItftStep *__restrict__ steps, int nsteps) {
-    constexpr int logC = ilog2c(C);
-    const u32 p = X.p;
+    constexpr int logC2 = ilog2c(C) - 1;
+    const u32 p = X.p, B = A::bound(p);
     for (int si = 0; si < nsteps; ++si) {
         const ItftStep st = steps[si];
         if (st.kind == ST_FULL) {
@@ -900,38 +915,230 @@ __device__ void coli_steps(const ColInvArgs &X, const ItftStep *__restrict__ ste
         }
         const bool upper = (st.kind == ST_PRE_RIGHT || st.kind == ST_PRE_LEFT);
         const int lo = upper ? st.m : 0, hi = upper ? st.h : st.m;
-        const int tasks = (hi - lo) << logC;
+        const int tasks = (hi - lo) << logC2;
         for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-            const u32 j = (u32)lo + ((u32)tau >> logC), c = (u32)tau & (C - 1);
-            u32 *X0 = X.sm + col_elem_addr<C, LAY>((u32)st.base + j, c);
-            u32 *X1 = X.sm + col_elem_addr<C, LAY>((u32)(st.base + st.h) + j, c);
-            const u32 x0 = A::to_canon(*X0, p), x1 = A::to_canon(*X1, p);
-            switch (st.kind) {
-                case ST_PRE_RIGHT: {
-                    const u32 l = mul_c(x0, st.hinv, p);
-                    if (st.zero) {
-                        *X0 = l;
-                        *X1 = l;
-                    } else {
-                        const u32 rc = mul_c(x1, st.r, p);
-                        const u32 cj = sub_c(l, rc, p);
-                        *X0 = cj;
-                        *X1 = sub_c(cj, rc, p);
-                    }
-                    break;
-                }
-                case ST_POST_RIGHT: {
-                    const u32 u = mul_c(x0, st.hinv, p);
-                    *X0 = mul_c(u + x1, st.inv2, p);
-                    *X1 = mul_c(u - x1 + p, st.i2r, p);
-                    break;
-                }
-                case ST_PRE_LEFT: *X0 = add_c(x0, mul_c(x1, st.r, p), p); break;
-                default: *X0 = sub_c(x0, mul_c(x1, st.r, p), p); break;
+            const u32 j = (u32)lo + ((u32)tau >> logC2), c = ((u32)tau & ((C >> 1) - 1)) << 1;
+            uint2 *P0 = reinterpret_cast<uint2 *>(X.sm + col_elem_addr<C, LAY>((u32)st.base + j, c));
+            uint2 *P1 = reinterpret_cast<uint2 *>(X.sm + col_elem_addr<C, LAY>((u32)(st.base + st.h) + j, c));
+            const uint2 v0 = *P0;
+            if (st.kind == ST_PRE_RIGHT && st.zero) {  // X_{j+h} = X_j
+                *P1 = v0;
+                continue;
             }
+            const uint2 v1 = *P1;
+            const u32 x[2] = {v0.x, v0.y}, y[2] = {v1.x, v1.y};
+            u32 o0[2], o1[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (st.kind == ST_POST_RIGHT) {  // ((x + y) / 2, (x - y) / (2r))
+                    o0[e] = half_mod(A::fwd_to_inv(x[e] + y[e], p), p);
+                    u32 t = shoup(x[e] - y[e] + B, st.i2r, p);
+                    o1[e] = A::lazy ? t : canon2(t, p);
+                } else {
+                    u32 t = shoup(y[e], st.r, p);
+                    if (!A::lazy) t = canon2(t, p);
+                    if (st.kind == ST_PRE_RIGHT) {  // X_j = x - r y; X_{j+h} = X_j - r y
+                        const u32 xj = A::fwd_to_inv(x[e] - t + B, p);
+                        o0[e] = xj;
+                        o1[e] = A::fwd_to_inv(xj - t + B, p);
+                    } else if (st.kind == ST_PRE_LEFT) {
+                        o0[e] = A::fwd_to_inv(x[e] + t, p);
+                    } else {  // ST_POST_LEFT
+                        o0[e] = A::fwd_to_inv(x[e] - t + B, p);
+                    }
+                }
+            }
+            *P0 = make_uint2(o0[0], o0[1]);
+            if (st.kind == ST_PRE_RIGHT || st.kind == ST_POST_RIGHT) *P1 = make_uint2(o1[0], o1[1]);
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------ truncated column inverse, one kernel
+// With k a multiple of T/8 (relaxed truncation; any k when T <= 8), every
+// bookkeeping record of the ITFT recursion sits in the top TOP = min(t, 3)
+// levels, and below them the recursion only inverts whole subtrees.  Those
+// subtree inverses are the deep levels of a plain full inverse restricted to
+// rows < k, so the kernel runs (1) the full inverse's passes over levels
+// [TOP, t) on rows < k, then (2) one pass in which each task holds the
+// 2^TOP rows j, j + T/2^TOP, ... of two columns in registers and runs the
+// top levels of the recursion there -- subtree butterflies, PRE/POST records
+// -- before storing the rows < k of the product.  k = T is the full inverse.
+
+// (a, b) -> ((a + b) / 2, (a - b) / (2r)) with ri = r^-1; [0, B) -> [0, B).
+template <class A>
+__device__ __forceinline__ void post_right(u32 &a, u32 &b, uint2 ri, u32 p) {
+    const u32 B = A::bound(p);
+    u32 d = shoup(a - b + B, ri, p);
+    if (!A::lazy) d = canon2(d, p);
+    const u32 s = A::fwd_to_inv(a + b, p);
+    a = half_mod(s, p);
+    b = half_mod(d, p);
+}
+
+// x, y: the M = 2^(levels) blocks of node (S, I) (two columns).  Unscaled
+// inverse of the whole node.
+template <class A, int M, int S, int I>
+__device__ __forceinline__ void top_full_inv(u32 *x, u32 *y, const uint2 *__restrict__ itw, u32 p) {
+    if constexpr (M >= 2) {
+        constexpr int h = M / 2;
+        top_full_inv<A, h, S + 1, 2 * I>(x, y, itw, p);
+        top_full_inv<A, h, S + 1, 2 * I + 1>(x + h, y + h, itw, p);
+        const uint2 w = __ldg(itw + tw_index(S, I));
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            A::gs(x[j], x[j + h], w, p);
+            A::gs(y[j], y[j + h], w, p);
+        }
+    }
+}
+
+// The ITFT recursion on node (S, I) of M blocks with k leading spectral
+// blocks (runtime); ZERO: the blocks past k hold zero coefficients.  Values
+// in [0, B); the spectral blocks arrive prescaled (see coli_steps).
+template <class A, int M, int S, int I, bool ZERO>
+__device__ __forceinline__ void itft_top(u32 *x, u32 *y, int k, const uint2 *__restrict__ tw,
+                                         const uint2 *__restrict__ itw, u32 p) {
+    if constexpr (M >= 2) {
+        if (k <= 0) return;
+        if (k == M) {
+            top_full_inv<A, M, S, I>(x, y, itw, p);
+            return;
+        }
+        constexpr int h = M / 2;
+        const u32 B = A::bound(p);
+        const uint2 r = __ldg(tw + tw_index(S, I));
+        if (k >= h) {
+            const int m = k - h;
+            top_full_inv<A, h, S + 1, 2 * I>(x, y, itw, p);
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                if (j < m) continue;
+                if (ZERO) {  // X_{j+h} = X_j
+                    x[j + h] = x[j];
+                    y[j + h] = y[j];
+                } else {  // X_j -= r X_{j+h}; X_{j+h} = X_j - r X_{j+h}
+                    u32 t = shoup(x[j + h], r, p), u = shoup(y[j + h], r, p);
+                    if (!A::lazy) {
+                        t = canon2(t, p);
+                        u = canon2(u, p);
+                    }
+                    x[j] = A::fwd_to_inv(x[j] - t + B, p);
+                    y[j] = A::fwd_to_inv(y[j] - u + B, p);
+                    x[j + h] = A::fwd_to_inv(x[j] - t + B, p);
+                    y[j + h] = A::fwd_to_inv(y[j] - u + B, p);
+                }
+            }
+            itft_top<A, h, S + 1, 2 * I + 1, false>(x + h, y + h, m, tw, itw, p);
+            const uint2 ri = __ldg(itw + tw_index(S, I));
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                if (j >= m) continue;
+                post_right<A>(x[j], x[j + h], ri, p);
+                post_right<A>(y[j], y[j + h], ri, p);
+            }
+        } else {
+            if (!ZERO) {
+#pragma unroll
+                for (int j = 0; j < h; ++j) {
+                    if (j < k) continue;
+                    u32 t = shoup(x[j + h], r, p), u = shoup(y[j + h], r, p);
+                    if (!A::lazy) {
+                        t = canon2(t, p);
+                        u = canon2(u, p);
+                    }
+                    x[j] = A::fwd_to_inv(x[j] + t, p);
+                    y[j] = A::fwd_to_inv(y[j] + u, p);
+                }
+            }
+            itft_top<A, h, S + 1, 2 * I, ZERO>(x, y, k, tw, itw, p);
+            if (!ZERO) {
+#pragma unroll
+                for (int j = 0; j < h; ++j) {
+                    if (j >= k) continue;
+                    u32 t = shoup(x[j + h], r, p), u = shoup(y[j + h], r, p);
+                    if (!A::lazy) {
+                        t = canon2(t, p);
+                        u = canon2(u, p);
+                    }
+                    x[j] = A::fwd_to_inv(x[j] - t + B, p);
+                    y[j] = A::fwd_to_inv(y[j] - u + B, p);
+                }
+            }
+        }
+    }
+}
+
+// Deep inverse pass (levels [S0, S0+R), S0 >= TOP) on rows < k only; a
+// group never straddles a block of T/2^TOP rows, so it is all in or all out.
+template <class A, int R, int C, int TL, int S0, int SRC>
+__device__ __forceinline__ void coli_deep_pass(const ColInvArgs &X) {
+    constexpr int logC2 = ilog2c(C) - 1, logM = TL - S0, logJ = logM - R;
+    constexpr int tasks = (1 << (TL - R)) << logC2;
+    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
+        const u32 G = (u32)tau >> logC2, c = ((u32)tau & ((C >> 1) - 1)) << 1;
+        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
+        const u32 r0 = (v << logM) | j;
+        if ((int)r0 >= X.k) continue;
+        const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
+        u32 x[1 << R], y[1 << R];
+        ct_load2<C, logJ, R>(x, y, X.sm, rc, H0);
+        grp_inv2<A, R>(x, y, X.itw, S0, v, X.p);
+        ct_store2<C, logJ, R>(x, y, X.sm, rc, H0);
+    }
+}
+
+template <class A, int C, int TL, int TOP, int I>
+__device__ __forceinline__ void coli_deep_passes(const ColInvArgs &X) {
+    using P = ColSplit<TL - TOP, I>;
+    if constexpr (I >= 0) {
+        coli_deep_pass<A, P::R, C, TL, TOP + P::S0, IO_SMEM>(X);
+        __syncthreads();
+        coli_deep_passes<A, C, TL, TOP, I - 1>(X);
+    }
+}
+
+template <int C, int LOGJ, int Q, int NQ>
+__device__ __forceinline__ void top_load2(u32 *x, u32 *y, const u32 *sm, u32 rc, u32 H0, int q) {
+    if constexpr (Q < NQ) {
+        if (Q < q) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(sm + CtAddr<C, LOGJ, Q>::at(rc, H0));
+            x[Q] = v.x;
+            y[Q] = v.y;
+        } else {
+            x[Q] = 0u;
+            y[Q] = 0u;
+        }
+        top_load2<C, LOGJ, Q + 1, NQ>(x, y, sm, rc, H0, q);
+    }
+}
+
+// Whole truncated (or, for k = T, full) column inverse of a loaded tile;
+// stores rows < k (entries < n) of the product.  Ends with a barrier.
+template <class A, int C, int TL>
+__device__ __forceinline__ void coli_tile_ct(const ColInvArgs &X) {
+    constexpr int TOP = TL < 3 ? TL : 3, NQ = 1 << TOP, LOGB = TL - TOP;
+    if constexpr (LOGB > 0) coli_deep_passes<A, C, TL, TOP, ColSplit<LOGB, 0>::np - 1>(X);
+    const int q = X.k >> LOGB;  // spectral blocks (k is a multiple of 2^LOGB)
+    constexpr int logC2 = ilog2c(C) - 1;
+    constexpr int tasks = (1 << LOGB) << logC2;
+    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
+        const u32 j = (u32)tau >> logC2, c = ((u32)tau & ((C >> 1) - 1)) << 1;
+        const u32 rc = j * C + c, H0 = tile_h<C>(j) * C;
+        u32 x[NQ], y[NQ];
+        top_load2<C, LOGB, 0, NQ>(x, y, X.sm, rc, H0, q);
+        itft_top<A, NQ, 0, 0, true>(x, y, q, X.tw, X.itw, X.p);
+        const u32 e0 = (j << X.logS) + X.c0 + c;
+#pragma unroll
+        for (int b = 0; b < NQ; ++b) {
+            if (b >= q) break;
+            const u32 e = e0 + ((u32)b << (LOGB + X.logS));
+            if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[b], X.p);
+            if ((int64_t)e + 1 < X.n) X.out[e + 1] = A::to_canon(y[b], X.p);
+        }
+    }
+    __syncthreads();
 }
 
 }  // namespace pm

@@ -175,7 +175,18 @@ int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st) {
         ctx->lazy = p < (1u << 30);
         ctx->m.p = p;
         ctx->m.pinv = pinv32(p);
-        ctx->tw = TwTables{nullptr, nullptr, 0};
+        ctx->tw = TwTables{nullptr, nullptr, 0, nullptr};
+        const std::vector<uint2> ps = pscale_table(p);
+        if (cudaMalloc(&ctx->pscale, ps.size() * sizeof(uint2)) != cudaSuccess) {
+            delete ctx;
+            return POLY_ENOMEM;
+        }
+        if (cudaMemcpy(ctx->pscale, ps.data(), ps.size() * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(ctx->pscale);
+            delete ctx;
+            return POLY_ECUDA;
+        }
+        ctx->tw.pscale = ctx->pscale;
         g_primes[key] = ctx;
     } else {
         ctx = it->second;
@@ -203,7 +214,10 @@ int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st) {
 //           recurse on it, then c_j = lo_j - r c_{j+h} (POST_LEFT).
 // Every step keeps the scale of its inputs, except a top-level node with all
 // M leaves, which is one unscaled full inverse (M times the coefficients).
-static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool zero, bool top,
+// A FULL record of size h leaves h times its coefficients, which the next
+// record multiplies by h^-1; with `prescaled` the leaves were already
+// multiplied by 1/h and h^-1 is recorded as 1.
+static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool zero, bool prescaled,
                       std::vector<ItftStep> &out) {
     const u32 p = ctx->p;
     if (k == 0) return;
@@ -226,7 +240,7 @@ static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool 
     st.base = base;
     st.h = h;
     st.r = shoup_pair(r, p);
-    st.hinv = shoup_pair(h_invmod((u32)(h % p), p), p);
+    st.hinv = shoup_pair(prescaled ? 1u : h_invmod((u32)(h % p), p), p);
     st.inv2 = shoup_pair(h_invmod(2, p), p);
     st.i2r = shoup_pair(h_invmod((u32)((u64)2 * r % p), p), p);
     if (k >= h) {
@@ -242,7 +256,7 @@ static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool 
         st.m = m;
         st.zero = zero ? 1 : 0;
         out.push_back(st);
-        steps_rec(ctx, s + 1, 2 * i + 1, base + h, h, m, false, false, out);
+        steps_rec(ctx, s + 1, 2 * i + 1, base + h, h, m, false, prescaled, out);
         st.kind = ST_POST_RIGHT;
         st.zero = 0;
         out.push_back(st);
@@ -252,19 +266,24 @@ static void steps_rec(PrimeCtx *ctx, int s, u32 i, int base, int M, int k, bool 
             st.kind = ST_PRE_LEFT;
             out.push_back(st);
         }
-        steps_rec(ctx, s + 1, 2 * i, base, h, k, zero, false, out);
+        steps_rec(ctx, s + 1, 2 * i, base, h, k, zero, prescaled, out);
         if (!zero) {
             st.kind = ST_POST_LEFT;
             out.push_back(st);
         }
     }
-    (void)top;
 }
 
-std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k) {
+std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k, bool prescaled) {
     std::vector<ItftStep> out;
-    steps_rec(ctx, 0, 0, 0, (int)M, (int)k, true, true, out);
+    steps_rec(ctx, 0, 0, 0, (int)M, (int)k, true, prescaled, out);
     return out;
+}
+
+std::vector<uint2> pscale_table(u32 p) {
+    std::vector<uint2> t(32);
+    for (int e = 0; e < 32; ++e) t[e] = scale_const(p, (u64)1 << e);
+    return t;
 }
 
 // Device copy of the step list for (T, k), cached per prime context.
@@ -277,7 +296,7 @@ int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int
         *nsteps = it->second.second;
         return POLY_OK;
     }
-    std::vector<ItftStep> v = itft_steps(ctx, T, k);
+    std::vector<ItftStep> v = itft_steps(ctx, T, k, true);
     if (!ctx->upload && cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking) != cudaSuccess)
         return POLY_ECUDA;
     if (ctx->arena_used + v.size() > ctx->arena_cap) {
@@ -351,7 +370,15 @@ Geometry make_geometry(int64_t n, int l, int sigma) {
     g.t = l - g.sigma;
     g.T = (int64_t)1 << g.t;
     g.n = n;
-    g.k = (n + g.S - 1) / g.S;
+    // Relaxed truncation (Section 5's relaxed parallel algorithms): the
+    // ceil(n/S) rows the product needs are rounded up to a multiple of
+    // T / 2^RELAX_LOG_T, so the truncated inverse has at most RELAX_LOG_T
+    // levels of bookkeeping records instead of t.  The extra rows hold true
+    // spectral values, and the product (degree < n) is unchanged.
+    const int64_t need = (n + g.S - 1) / g.S;
+    const int64_t gran = g.t > RELAX_LOG_T ? g.T >> RELAX_LOG_T : 1;
+    g.k = (need + gran - 1) / gran * gran;
+    if (g.k > g.T) g.k = g.T;
     return g;
 }
 
@@ -405,7 +432,6 @@ int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t
     d->steps = st;
     d->nsteps = ns;
     d->prune = prune ? 1 : 0;
-    d->cscale = scale_const(ctx->p, (u64)S * (k == T ? T : 1));
     return POLY_OK;
 }
 
@@ -429,7 +455,6 @@ int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t
     d->steps = st;
     d->nsteps = ns;
     d->prune = prune ? 1 : 0;
-    d->cscale = scale_const(ctx->p, (u64)g.S * (g.k == g.T ? (u64)g.T : 1));
     return POLY_OK;
 }
 
@@ -647,7 +672,7 @@ int tft_plan_create(uint32_t p, uint32_t root, int64_t z, int64_t n, tft_plan **
     pl->l = l;
     pl->L = (int64_t)1 << l;
     pl->ctx = ctx;
-    pl->steps = itft_steps(ctx, pl->L, n);
+    pl->steps = itft_steps(ctx, pl->L, n, false);
     *out = pl;
     return POLY_OK;
 }

@@ -17,6 +17,7 @@ struct PrimeCtx {
     ModParams m{};
     TwTables tw{};
     uint2 *fwd = nullptr, *inv = nullptr;
+    uint2 *pscale = nullptr;  // 32 Shoup pairs of 2^32 * 2^-e
     std::vector<uint2 *> retired;
     std::map<std::pair<int64_t, int64_t>, std::pair<const ItftStep *, int>> steps;
     // Step lists live in device arenas filled through a private stream, so
@@ -37,7 +38,12 @@ int ceil_log2(int64_t n);
 
 int validate_prime(u32 p, u32 *root);
 int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st);
-std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k);
+// prescaled: the spectral rows arrive multiplied by 1/h for their FULL
+// record (the product paths fold that into the pointwise constant), so the
+// records carry h^-1 = 1; otherwise (tft plans) h^-1 is the true inverse.
+std::vector<ItftStep> itft_steps(PrimeCtx *ctx, int64_t M, int64_t k, bool prescaled);
+// The pointwise constants 2^32 * 2^-e mod p, e = 0..31.
+std::vector<uint2> pscale_table(u32 p);
 int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int *nsteps);
 
 Schedule default_schedule(int l);

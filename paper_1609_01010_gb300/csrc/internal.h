@@ -20,7 +20,8 @@ typedef uint64_t u64;
 struct TwTables {
     const uint2 *fwd;
     const uint2 *inv;
-    int lmax;  // entries [1, 2^lmax) are valid
+    int lmax;             // entries [1, 2^lmax) are valid
+    const uint2 *pscale;  // pscale[e] = Shoup pair of 2^32 * 2^-e mod p, e < 32
 };
 
 __host__ __device__ inline uint32_t tw_index(int level, uint32_t node) { return (1u << level) + node; }
@@ -56,7 +57,7 @@ struct ItftStep {
 // Block-relaxed decomposition of a length-L transform: L = T * S, rows of S
 // words.  The top t = log2 T tree levels act on whole rows (the column
 // stage); the bottom sigma = log2 S levels act inside one row (row stage).
-// Truncation is applied at row granularity: k = ceil(n / S) rows are needed.
+// Truncation is applied at row granularity: k >= ceil(n / S) rows are computed.
 struct Geometry {
     int l, t, sigma;
     int64_t L, S, T, k, n;
@@ -70,6 +71,9 @@ constexpr int SMALL_MAX_LOG_L = SMALL_LOG_S + SMALL_MAX_LOG_T;
 // Large products: rows of S = 2^sigma (11..13) words handled by one CTA each,
 // column tiles of C words handled by one CTA each, T <= 1024 rows.
 constexpr int LARGE_MAX_LOG_T = 10;
+// Rows computed by the three-kernel path: ceil(n/S) rounded up to a multiple
+// of T / 2^RELAX_LOG_T (see make_geometry).
+constexpr int RELAX_LOG_T = 3;
 
 // Shared memory of one row of the row stage: both operands' rows (2 S words)
 // and the row's twiddles (S entries of 8 bytes, entry 0 unused).
@@ -107,7 +111,6 @@ struct SmallDesc {
     const ItftStep *steps;
     int32_t nsteps;
     int32_t prune;  // 0: compute every butterfly (the zero-padded comparator)
-    uint2 cscale;   // 2^32 * (row/column scale)^-1 mod p, Shoup pair
 };
 // d_desc: device array of `count` descriptors, or NULL to use *h_one (count 1).
 cudaError_t launch_small(bool lazy, int logT, const SmallDesc *d_desc, const SmallDesc *h_one, int count,
@@ -122,7 +125,6 @@ struct LargeDesc {
     const ItftStep *steps;
     int32_t nsteps;
     int32_t prune;  // 0: compute every butterfly (the zero-padded comparator)
-    uint2 cscale;
 };
 // ev: NULL, or 4 events recorded before the column stage, after it, after
 // the row stage and after the ITFT column stage (profiling).

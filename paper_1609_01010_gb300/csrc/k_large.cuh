@@ -7,8 +7,9 @@
 //   k_row_fused grid (k):      one CTA per needed row: remaining sigma levels
 //               of both operands, pointwise product with the scale folded in,
 //               unscaled inverse of the sigma levels; overwrites wa's row.
-//   k_col_itft  grid (S/C):    ITFT column stage from the step list, then
-//               the first n outputs reduced to [0, p).
+//   k_col_itft  grid (S/C):    ITFT column stage (a full inverse when k = T,
+//               else the truncated one of coli_tile_ct), then the first n
+//               outputs reduced to [0, p).
 // Each kernel reads its inputs once from HBM/L2 and writes its outputs once.
 #pragma once
 #include "bodies.cuh"

@@ -8,7 +8,8 @@
 //                 operands' column stages, then the product's rows);
 //   g_na_tw       the twiddle tables of the two built-in primes;
 //   g_na_steps    the ITFT step lists of every (T, k) the entry point can meet;
-//   g_na_pow      power tables used once to build the twiddles.
+//   g_na_pow      power tables used once to build the twiddles;
+//   g_na_pscale   the pointwise scale constants of the two primes.
 // In host code a static __device__ array's name is only a host-side
 // stand-in, so the device addresses are fetched once per device with
 // cudaGetSymbolAddress (with that device current) and passed to the kernels.
@@ -40,12 +41,14 @@ static __device__ __align__(256) uint32_t g_na_scratch[NA_SCRATCH_WORDS];
 static __device__ __align__(256) uint2 g_na_tw[2 * 2 * NA_TW_ENTRIES];  // prime x {fwd, inv}
 static __device__ __align__(256) ItftStep g_na_steps[NA_MAX_STEPS];
 static __device__ __align__(256) uint32_t g_na_pow[2 * (4096 + NA_POW_HI)];
+static __device__ __align__(256) uint2 g_na_pscale[2 * 32];
 
 struct NaDevice {
     bool ready = false;
     u32 *scratch = nullptr;
     uint2 *tw = nullptr;
     ItftStep *steps = nullptr;
+    uint2 *pscale = nullptr;
     std::map<std::pair<int64_t, int64_t>, std::pair<int, int>> lists[2];  // (T, k) -> (offset, count)
 };
 
@@ -77,6 +80,9 @@ static int na_setup(int dev, NaDevice &D) {
     e = cudaGetSymbolAddress(&ptr, g_na_pow);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(powers)");
     u32 *pow_dev = (u32 *)ptr;
+    e = cudaGetSymbolAddress(&ptr, g_na_pscale);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scales)");
+    D.pscale = (uint2 *)ptr;
 
     std::vector<ItftStep> all;
     for (int pi = 0; pi < 2; ++pi) {
@@ -105,13 +111,16 @@ static int na_setup(int dev, NaDevice &D) {
         e = launch_build_tw(fwd, inv, lmax, p, pw_dev, pw_dev + 4096, nullptr);
         if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "twiddle build");
+        const std::vector<uint2> ps = pscale_table(p);
+        e = cudaMemcpy(D.pscale + pi * 32, ps.data(), 32 * sizeof(uint2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "scale table");
         // step lists: one-CTA path (T = 1..16 rows of 512) and three-kernel path
         // (rows of 2^NA_SIGMA, T = 16..128)
         PrimeCtx tmp;
         tmp.p = p;
         tmp.root = root;
         auto add = [&](int64_t T, int64_t k) {
-            std::vector<ItftStep> v = itft_steps(&tmp, T, k);
+            std::vector<ItftStep> v = itft_steps(&tmp, T, k, true);
             D.lists[pi][std::make_pair(T, k)] = std::make_pair((int)all.size(), (int)v.size());
             all.insert(all.end(), v.begin(), v.end());
         };
@@ -160,6 +169,7 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
     tw.fwd = D->tw + (size_t)pi * 2 * NA_TW_ENTRIES;
     tw.inv = tw.fwd + NA_TW_ENTRIES;
     tw.lmax = NA_MAX_LOG_L;
+    tw.pscale = D->pscale + pi * 32;
     const int l = ceil_log2(n);
     cudaStream_t st = (cudaStream_t)stream;
     if (l <= SMALL_MAX_LOG_L) {
@@ -180,7 +190,6 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
         d.steps = D->steps + ls.first;
         d.nsteps = ls.second;
         d.prune = 1;
-        d.cscale = scale_const(p, (u64)S * (k == T ? T : 1));
         e = launch_small(lazy, logT, nullptr, &d, 1, m, tw, st);
         return e == cudaSuccess ? POLY_OK : cuda_fail(e, "one-CTA product launch");
     }
@@ -199,7 +208,6 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
     d.steps = D->steps + ls.first;
     d.nsteps = ls.second;
     d.prune = 1;
-    d.cscale = scale_const(p, (u64)g.S * (g.k == g.T ? (u64)g.T : 1));
     e = launch_large(lazy, d, Schedule{NA_SIGMA, NA_C}, m, tw, st);
     return e == cudaSuccess ? POLY_OK : cuda_fail(e, "three-kernel product launch");
 }
