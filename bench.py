@@ -392,58 +392,101 @@ def batched(dev, stream, B, reps=5):
             "plain": "one polymul_mod_async per product (its own 1 or 3 kernel launches)"}
 
 
-def serving(dev, B, seconds, rate=20000.0, budget=8 << 30):
-    """Poisson stream into the server; latency = submit -> GPU completion."""
+def serve_run(dev, B, mode, t_arr, prime, da_, db_, pools, budget, check_every=997):
+    """One request stream through a server in `mode`; latency = submit -> GPU completion."""
     import torch
-    import oracle
-    t_arr, prime, da_, db_ = W.request_stream(rate=rate, seconds=seconds)
     pool_words = 1 << 21
-    pools = {q: dev_u32(W.coeffs(W.SEED_BASE + 50 + i, pool_words + (1 << 20) + 2, q), dev)
-             for i, q in enumerate((W.P1, W.P2))}
-    pool_host = {q: host_u32(pools[q]) for q in pools}
     arena_words = 1 << 28  # 1 GiB output ring (outputs of unchecked requests may be overwritten)
     arena = torch.empty(arena_words, dtype=torch.int32, device=dev)
     rng = np.random.default_rng(5)
-    srv = B.polymul_server_create(budget, 4)
+    srv = B.polymul_server_create(budget, 4, mode)
     checks = []
     head = 0
-    t0 = time.perf_counter()
-    tickets = []
+    # every request's addresses are computed before the clock starts, so the
+    # submit loop costs one library call per request
+    reqs = []
     for i in range(len(t_arr)):
-        while time.perf_counter() - t0 < t_arr[i]:
-            pass
         q = int(prime[i])
         za, zb = int(da_[i]) + 1, int(db_[i]) + 1
         n = za + zb - 1
         offa, offb = int(rng.integers(0, pool_words)), int(rng.integers(0, pool_words))
-        pa = pools[q][offa:offa + za]
-        pb = pools[q][offb:offb + zb]
-        if i % 997 == 0:
+        if i % check_every == 0:
             pc = torch.empty(n, dtype=torch.int32, device=dev)
             checks.append((q, offa, za, offb, zb, pc))
+            c_ptr = pc.data_ptr()
         else:
             if head + n > arena_words:
                 head = 0
-            pc = arena[head:head + n]
+            c_ptr = arena.data_ptr() + 4 * head
             head += n
-        tickets.append(B.polymul_server_submit(srv, q, pa, za - 1, pb, zb - 1, pc))
+        reqs.append((float(t_arr[i]), q, pools[q].data_ptr() + 4 * offa, za - 1, pools[q].data_ptr() + 4 * offb,
+                     zb - 1, c_ptr))
+    submit = B.polymul_server_submit
+    tickets = []
+    t0 = time.perf_counter()
+    for ta, q, pa, da, pb, db, pc in reqs:
+        while time.perf_counter() - t0 < ta:
+            pass
+        tickets.append(submit(srv, q, pa, da, pb, db, pc))
     t_sub = time.perf_counter() - t0
     for t in tickets:
         B.polymul_server_wait(srv, t, 120000)
     t_all = time.perf_counter() - t0
     stats = B.polymul_server_stats(srv)
     B.polymul_server_destroy(srv)
-    ok = True
-    for q, offa, za, offb, zb, pc in checks[:8]:
-        want = oracle.polymul_tft(q, pool_host[q][offa:offa + za], pool_host[q][offb:offb + zb])
-        ok = ok and bool(np.array_equal(host_u32(pc), want))
+    del arena
+    return stats, t_sub, t_all, checks
+
+
+def serving(dev, B, seconds, rate=20000.0, budget=8 << 30, burst=20000):
+    """Workload 5 through the server (one batched launch per admitted group,
+    POLY_SERVE_BATCH), beside the same stream served one plain product per
+    request (POLY_SERVE_PLAIN); then a saturation burst (all requests
+    submitted at once) for each mode."""
+    import oracle
+    t_arr, prime, da_, db_ = W.request_stream(rate=rate, seconds=seconds)
+    pool_words = 1 << 21
+    pools = {q: dev_u32(W.coeffs(W.SEED_BASE + 50 + i, pool_words + (1 << 20) + 2, q), dev)
+             for i, q in enumerate((W.P1, W.P2))}
+    pool_host = {q: host_u32(pools[q]) for q in pools}
     n_total = int((da_ + db_ + 1).sum())
-    return {"workload": f"Poisson {rate:.0f} req/s for {seconds} s, p in {{469762049, 2013265921}}, "
-                        "degrees log-uniform in [256, 2^20], 8 GB admission budget, 4 streams",
-            "requests": len(t_arr), "submit_s": t_sub, "drain_s": t_all, "p50_us": stats["p50_us"],
-            "p90_us": stats["p90_us"], "p99_us": stats["p99_us"], "max_us": stats["max_us"],
-            "mean_us": stats["mean_us"], "throughput_req_per_s": len(t_arr) / t_all,
-            "coeffs_per_s": n_total / t_all, "checked_against_oracle": min(8, len(checks)), "checks_ok": ok}
+    out = {"workload": f"Poisson {rate:.0f} req/s for {seconds} s, p in {{469762049, 2013265921}}, "
+                       "degrees log-uniform in [256, 2^20], 8 GB admission budget, 4 streams",
+           "requests": len(t_arr)}
+    ok = True
+    nchk = 0
+    # warm-up (untimed): a burst of 2000 requests through each mode loads
+    # every kernel variant the stream meets
+    w = min(2000, len(t_arr))
+    for mode in (B.SERVE_BATCH, B.SERVE_PLAIN):
+        serve_run(dev, B, mode, np.zeros(w), prime[:w], da_[:w], db_[:w], pools, budget, check_every=10 ** 9)
+    for name, mode in (("batch", B.SERVE_BATCH), ("plain", B.SERVE_PLAIN)):
+        stats, t_sub, t_all, checks = serve_run(dev, B, mode, t_arr, prime, da_, db_, pools, budget)
+        out[name] = {"p50_us": stats["p50_us"], "p90_us": stats["p90_us"], "p99_us": stats["p99_us"],
+                     "max_us": stats["max_us"], "mean_us": stats["mean_us"], "submit_s": t_sub, "drain_s": t_all,
+                     "throughput_req_per_s": len(t_arr) / t_all, "coeffs_per_s": n_total / t_all}
+        for q, offa, za, offb, zb, pc in checks[:3]:
+            want = oracle.polymul_tft(q, pool_host[q][offa:offa + za], pool_host[q][offb:offb + zb])
+            ok = ok and bool(np.array_equal(host_u32(pc), want))
+            nchk += 1
+    # saturation: the first `burst` requests of the stream submitted back to back
+    m = min(burst, len(t_arr))
+    zeros = np.zeros(m)
+    sat = {}
+    for name, mode in (("batch", B.SERVE_BATCH), ("plain", B.SERVE_PLAIN)):
+        stats, t_sub, t_all, _ = serve_run(dev, B, mode, zeros, prime[:m], da_[:m], db_[:m], pools, budget,
+                                           check_every=10 ** 9)
+        sat[name] = {"req_per_s": m / t_all, "coeffs_per_s": int((da_[:m] + db_[:m] + 1).sum()) / t_all,
+                     "p50_us": stats["p50_us"], "p99_us": stats["p99_us"]}
+    out["saturation"] = dict(requests=m, **sat)
+    out["p50_us"] = out["batch"]["p50_us"]
+    out["p99_us"] = out["batch"]["p99_us"]
+    out["p50_vs_plain"] = out["plain"]["p50_us"] / out["batch"]["p50_us"]
+    out["p99_vs_plain"] = out["plain"]["p99_us"] / out["batch"]["p99_us"]
+    out["saturation_vs_plain"] = sat["batch"]["req_per_s"] / sat["plain"]["req_per_s"]
+    out["checked_against_oracle"] = nchk
+    out["checks_ok"] = ok
+    return out
 
 
 def main():
@@ -453,7 +496,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load before the timed region")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--skip", default="", help="comma list of parts to skip: e2e,cpu,padded,sweep,batched,serving")
     args = ap.parse_args()
     if args.warmup < 3:

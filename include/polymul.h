@@ -227,15 +227,21 @@ int polymul_load_schedules(const char *json_path);
 /* ---------------------------------------------------------------- serving */
 typedef struct polymul_server polymul_server;
 
+/* Dispatch modes of the server. */
+#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 as one persistent batched launch, larger ones plain */
+#define POLY_SERVE_PLAIN 1 /* every request as its own plain product (the comparator) */
+
 /*
- * A continuous-batching server on the current device.  Requests are admitted
- * while the bytes they hold (inputs, output and workspace) fit in
- * mem_budget_bytes; the rest wait in arrival order.  Admitted requests are
- * packed into persistent-kernel launches on `n_streams` streams, so work
- * admitted while other work runs overlaps on the GPU.  Twiddle tables and
- * plans for 469762049 and 2013265921 are made resident at creation.
+ * A continuous-batching server on the current device (the paper has no
+ * serving layer).  Requests are admitted while the bytes they hold (inputs,
+ * output and workspace) fit in mem_budget_bytes; the rest wait in arrival
+ * order.  A free stream (of `n_streams`) takes all admissible queued requests
+ * of one prime as a group and runs them as `mode` says, so work admitted while
+ * other work runs overlaps on the GPU.  Twiddle tables and plans for
+ * 469762049 and 2013265921 are made resident at creation.  POLY_EINVAL for a
+ * zero budget, n_streams outside [1, 64] or an unknown mode.
  */
-int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server **out);
+int polymul_server_create(size_t mem_budget_bytes, int n_streams, int mode, polymul_server **out);
 
 /*
  * Submit c = a * b mod p.  a, b, c: device buffers owned by the caller, which

@@ -57,7 +57,7 @@ _SIGS = {
     "polymul_mod_batched_plain": (ctypes.c_int, [u32, i64, vp, I64P, vp, I64P, vp, I64P, vp]),
     "polymul_autotune": (ctypes.c_int, [u32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
     "polymul_load_schedules": (ctypes.c_int, [ctypes.c_char_p]),
-    "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
+    "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
     "polymul_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, i64]),
@@ -266,9 +266,12 @@ def polymul_load_schedules(json_path: str) -> None:
 
 
 # ------------------------------------------------------------ serving
-def polymul_server_create(mem_budget_bytes: int, n_streams: int = 4) -> int:
+SERVE_BATCH, SERVE_PLAIN = 0, 1
+
+
+def polymul_server_create(mem_budget_bytes: int, n_streams: int = 4, mode: int = SERVE_BATCH) -> int:
     h = vp()
-    _check(lib().polymul_server_create(mem_budget_bytes, n_streams, ctypes.byref(h)), "polymul_server_create")
+    _check(lib().polymul_server_create(mem_budget_bytes, n_streams, mode, ctypes.byref(h)), "polymul_server_create")
     return h.value
 
 

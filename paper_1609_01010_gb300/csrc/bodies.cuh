@@ -59,7 +59,7 @@ __device__ __forceinline__ void small_body(const SmallDesc &d, ModParams m, TwTa
         srow_inv<A, SMALL_LOG_S, NP - 1>(xa, sa + w * S, lane, LOGT, (u32)w, tw.inv, p);
     }
     __syncthreads();
-    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p, tw.fwd};
+    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p, tw.fwd, nullptr};
     coli_steps<A, S, LAY_SWZ>(Y, d.steps, d.nsteps);
     for (int64_t e = threadIdx.x; e < d.n; e += blockDim.x) d.c[e] = A::to_canon(sa[swz((u32)e)], p);
     __syncthreads();
@@ -238,7 +238,7 @@ template <class A, int C>
 __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
     const u32 c0 = (u32)tile * C;
     const int T = (int)d.g.T, k = (int)d.g.k;
-    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p, tw.fwd};
+    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p, tw.fwd, nullptr};
     if (d.g.t == 0) {
         for (int c = threadIdx.x; c < C; c += blockDim.x)
             if ((int64_t)(c0 + c) < d.n) d.c[c0 + c] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(0, c)], m.p);
@@ -256,8 +256,9 @@ __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *
 // Column inverse of a loaded tile with compile-time pass shapes: the full
 // inverse when k = T, the truncated one otherwise (k a multiple of T/8).
 template <class A, int C, int TL>
-__device__ __forceinline__ void coli_compute_ct(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
-    const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p, tw.fwd};
+__device__ __forceinline__ void coli_compute_ct(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw,
+                                             const uint2 *top) {
+    const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p, tw.fwd, top};
     coli_tile_ct<A, C, TL>(X);
 }
 

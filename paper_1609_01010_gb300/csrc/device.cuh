@@ -81,9 +81,20 @@ __device__ __forceinline__ void grp_fwd_cp(u32 *x, const uint2 *__restrict__ tw,
     }
 }
 
-// Two columns at once (x, y), sharing the twiddle loads.
+// A twiddle pair from shared memory (the compile-time-shaped column kernels
+// stage the column tree's twiddles there once per CTA).
+__device__ __forceinline__ uint2 lds_tw(const uint2 *p) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "r"((u32)__cvta_generic_to_shared(p)));
+    return v;
+}
+
+// Two columns at once (x, y), sharing the twiddle loads; tw is the shared
+// memory copy of the table (lds_tw).
 template <class A, int R>
-__device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *__restrict__ tw, int lev0, u32 node0, u32 p,
+__device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *tw, int lev0, u32 node0, u32 p,
                                             u32 copymask) {
 #pragma unroll
     for (int d = 0; d < R; ++d) {
@@ -100,7 +111,7 @@ __device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *__restr
         } else {
 #pragma unroll
             for (int e = 0; e < (1 << d); ++e) {
-                const uint2 w = __ldg(tw + tw_index(lev0 + d, (node0 << d) + e));
+                const uint2 w = lds_tw(tw + tw_index(lev0 + d, (node0 << d) + e));
 #pragma unroll
                 for (int jj = 0; jj < half; ++jj) {
                     const int lo = e * 2 * half + jj;
@@ -113,13 +124,13 @@ __device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *__restr
 }
 
 // Node E at relative depth D of an R-level inverse group, then the nodes
-// after it; template recursion keeps every array index a constant.
+// after it; template recursion keeps every array index a constant.  itw is
+// the shared memory copy of the inverse table (lds_tw).
 template <class A, int R, int D, int E>
-__device__ __forceinline__ void grp_inv2_nodes(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0,
-                                               u32 p) {
+__device__ __forceinline__ void grp_inv2_nodes(u32 *x, u32 *y, const uint2 *itw, int lev0, u32 node0, u32 p) {
     if constexpr (E < (1 << D)) {
         constexpr int half = 1 << (R - 1 - D);
-        const uint2 w = __ldg(itw + tw_index(lev0 + D, (node0 << D) + E));
+        const uint2 w = lds_tw(itw + tw_index(lev0 + D, (node0 << D) + E));
 #pragma unroll
         for (int jj = 0; jj < half; ++jj) {
             A::gs(x[E * 2 * half + jj], x[E * 2 * half + jj + half], w, p);
@@ -130,7 +141,7 @@ __device__ __forceinline__ void grp_inv2_nodes(u32 *x, u32 *y, const uint2 *__re
 }
 
 template <class A, int R, int D = R - 1>
-__device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
+__device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *itw, int lev0, u32 node0, u32 p) {
     if constexpr (D >= 0) {
         grp_inv2_nodes<A, R, D, 0>(x, y, itw, lev0, node0, p);
         grp_inv2<A, R, D - 1>(x, y, itw, lev0, node0, p);
@@ -652,6 +663,9 @@ struct ColInvArgs {
     const uint2 *itw;
     u32 p;
     const uint2 *tw;  // forward table (r of the truncated inverse's records)
+    // coli_tile_ct only: the top three levels' twiddles in shared memory,
+    // top[e] = fwd[e] and top[8 + e] = inv[e] for tree nodes e = 1..7
+    const uint2 *top;
 };
 
 // Inverse pass of R levels [lev0, lev0+R) of the subtree rooted at (s_root,
@@ -836,56 +850,6 @@ __device__ __forceinline__ void colf_tile_ct(const ColFwdArgs &X) {
     colf_passes_ct<A, C, TL, 0>(X, copymask);
 }
 
-// Inverse pass of R levels at depth S0 of a full TL-level column inverse
-// (two adjacent columns per task).
-template <class A, int R, int C, int TL, int S0, int DST>
-__device__ __forceinline__ void coli_pass_ct(const ColInvArgs &X) {
-    constexpr int logC2 = ilog2c(C) - 1, logM = TL - S0, logJ = logM - R;
-    constexpr int tasks = (1 << (TL - R)) << logC2;
-    for (int tau = threadIdx.x; tau < tasks; tau += blockDim.x) {
-        const u32 G = (u32)tau >> logC2, c = ((u32)tau & ((C >> 1) - 1)) << 1;
-        const u32 v = G >> logJ, j = G & ((1u << logJ) - 1u);
-        const u32 r0 = (v << logM) | j;
-        const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
-        u32 x[1 << R], y[1 << R];
-        ct_load2<C, logJ, R>(x, y, X.sm, rc, H0);
-        grp_inv2<A, R>(x, y, X.itw, S0, v, X.p);
-        if constexpr (DST == IO_GLOBAL) {
-            const u32 e0 = (r0 << X.logS) + X.c0 + c;
-            const int sh = logJ + X.logS;
-#pragma unroll
-            for (int q = 0; q < (1 << R); ++q) {
-                const u32 e = e0 + ((u32)q << sh);
-                if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[q], X.p);
-                if ((int64_t)e + 1 < X.n) X.out[e + 1] = A::to_canon(y[q], X.p);
-            }
-        } else {
-            ct_store2<C, logJ, R>(x, y, X.sm, rc, H0);
-        }
-    }
-}
-
-template <class A, int C, int TL, int I>
-__device__ __forceinline__ void coli_passes_ct(const ColInvArgs &X) {
-    using P = ColSplit<TL, I>;
-    if constexpr (I >= 0) {
-        if constexpr (I == 0) {
-            coli_pass_ct<A, P::R, C, TL, P::S0, IO_GLOBAL>(X);
-        } else {
-            coli_pass_ct<A, P::R, C, TL, P::S0, IO_SMEM>(X);
-        }
-        __syncthreads();
-        coli_passes_ct<A, C, TL, I - 1>(X);
-    }
-}
-
-// Full unscaled inverse of a loaded TL-level tile, deepest pass first; the
-// top pass writes the product.  Ends with a barrier.
-template <class A, int C, int TL>
-__device__ __forceinline__ void coli_full_ct(const ColInvArgs &X) {
-    coli_passes_ct<A, C, TL, ColSplit<TL, 0>::np - 1>(X);
-}
-
 template <int C, int LAY>
 __device__ __forceinline__ u32 col_elem_addr(u32 r, u32 c) {
     if constexpr (LAY == LAY_SWZ) return swz(r * C + c);
@@ -980,12 +944,12 @@ __device__ __forceinline__ void post_right(u32 &a, u32 &b, uint2 ri, u32 p) {
 // x, y: the M = 2^(levels) blocks of node (S, I) (two columns).  Unscaled
 // inverse of the whole node.
 template <class A, int M, int S, int I>
-__device__ __forceinline__ void top_full_inv(u32 *x, u32 *y, const uint2 *__restrict__ itw, u32 p) {
+__device__ __forceinline__ void top_full_inv(u32 *x, u32 *y, const uint2 *top, u32 p) {
     if constexpr (M >= 2) {
         constexpr int h = M / 2;
-        top_full_inv<A, h, S + 1, 2 * I>(x, y, itw, p);
-        top_full_inv<A, h, S + 1, 2 * I + 1>(x + h, y + h, itw, p);
-        const uint2 w = __ldg(itw + tw_index(S, I));
+        top_full_inv<A, h, S + 1, 2 * I>(x, y, top, p);
+        top_full_inv<A, h, S + 1, 2 * I + 1>(x + h, y + h, top, p);
+        const uint2 w = top[8 + (1 << S) + I];
 #pragma unroll
         for (int j = 0; j < h; ++j) {
             A::gs(x[j], x[j + h], w, p);
@@ -998,20 +962,19 @@ __device__ __forceinline__ void top_full_inv(u32 *x, u32 *y, const uint2 *__rest
 // blocks (runtime); ZERO: the blocks past k hold zero coefficients.  Values
 // in [0, B); the spectral blocks arrive prescaled (see coli_steps).
 template <class A, int M, int S, int I, bool ZERO>
-__device__ __forceinline__ void itft_top(u32 *x, u32 *y, int k, const uint2 *__restrict__ tw,
-                                         const uint2 *__restrict__ itw, u32 p) {
+__device__ __forceinline__ void itft_top(u32 *x, u32 *y, int k, const uint2 *top, u32 p) {
     if constexpr (M >= 2) {
         if (k <= 0) return;
         if (k == M) {
-            top_full_inv<A, M, S, I>(x, y, itw, p);
+            top_full_inv<A, M, S, I>(x, y, top, p);
             return;
         }
         constexpr int h = M / 2;
         const u32 B = A::bound(p);
-        const uint2 r = __ldg(tw + tw_index(S, I));
+        const uint2 r = top[(1 << S) + I];
         if (k >= h) {
             const int m = k - h;
-            top_full_inv<A, h, S + 1, 2 * I>(x, y, itw, p);
+            top_full_inv<A, h, S + 1, 2 * I>(x, y, top, p);
 #pragma unroll
             for (int j = 0; j < h; ++j) {
                 if (j < m) continue;
@@ -1030,8 +993,8 @@ __device__ __forceinline__ void itft_top(u32 *x, u32 *y, int k, const uint2 *__r
                     y[j + h] = A::fwd_to_inv(y[j] - u + B, p);
                 }
             }
-            itft_top<A, h, S + 1, 2 * I + 1, false>(x + h, y + h, m, tw, itw, p);
-            const uint2 ri = __ldg(itw + tw_index(S, I));
+            itft_top<A, h, S + 1, 2 * I + 1, false>(x + h, y + h, m, top, p);
+            const uint2 ri = top[8 + (1 << S) + I];
 #pragma unroll
             for (int j = 0; j < h; ++j) {
                 if (j >= m) continue;
@@ -1052,7 +1015,7 @@ __device__ __forceinline__ void itft_top(u32 *x, u32 *y, int k, const uint2 *__r
                     y[j] = A::fwd_to_inv(y[j] + u, p);
                 }
             }
-            itft_top<A, h, S + 1, 2 * I, ZERO>(x, y, k, tw, itw, p);
+            itft_top<A, h, S + 1, 2 * I, ZERO>(x, y, k, top, p);
             if (!ZERO) {
 #pragma unroll
                 for (int j = 0; j < h; ++j) {
@@ -1128,7 +1091,7 @@ __device__ __forceinline__ void coli_tile_ct(const ColInvArgs &X) {
         const u32 rc = j * C + c, H0 = tile_h<C>(j) * C;
         u32 x[NQ], y[NQ];
         top_load2<C, LOGB, 0, NQ>(x, y, X.sm, rc, H0, q);
-        itft_top<A, NQ, 0, 0, true>(x, y, q, X.tw, X.itw, X.p);
+        itft_top<A, NQ, 0, 0, true>(x, y, q, X.top, X.p);
         const u32 e0 = (j << X.logS) + X.c0 + c;
 #pragma unroll
         for (int b = 0; b < NQ; ++b) {

@@ -17,15 +17,33 @@
 namespace pm {
 
 constexpr int COL_THREADS = 128;
-constexpr size_t COL_SMEM_MAX = 128 * 1024;  // 2 * T * C * 4 bytes (schedule_valid's bound)
+// 2 * T * C * 4 bytes of tiles (at most 128 KB, schedule_valid's bound) and
+// up to 16 KB of column twiddles.
+constexpr size_t COL_SMEM_MAX = 144 * 1024;
 
 // Persistent column kernels: each CTA walks items blockIdx.x, +gridDim.x, ...
 // and double-buffers them: the cp.async copies of the next item are in
 // flight while the current one computes.  TL = column depth (compile time).
+// Copies the column tree's 2^TL table entries (levels < TL) into shared
+// memory behind the two tile buffers; the first barrier of the tile loop
+// publishes it.
+template <int TL>
+__device__ __forceinline__ uint2 *stage_col_tw(u32 *smem, u32 words, const uint2 *table) {
+    uint2 *s = reinterpret_cast<uint2 *>(smem + 2 * words);
+    for (int i = threadIdx.x; i < (1 << TL); i += blockDim.x) s[i] = i ? __ldg(table + i) : make_uint2(0u, 0u);
+    return s;
+}
+
+template <int C, int TL>
+constexpr size_t col_smem_bytes() {
+    return (size_t)2 * ((size_t)C << TL) * sizeof(u32) + ((size_t)8 << TL);
+}
+
 template <class A, int C, int TL>
 __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     const u32 words = (u32)C << TL;
+    tw.fwd = stage_col_tw<TL>(smem, words, tw.fwd);
     const int items = 2 * (int)(d.g.S / C);  // (tile, operand) pairs
     int it = blockIdx.x;
     if (it < items) colf_load<C>(d, it >> 1, it & 1, smem);
@@ -40,15 +58,28 @@ __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, M
     }
 }
 
+// Resident CTAs per SM the row kernel is compiled for: what its shared
+// memory (2 S words of rows + S twiddles of 8 bytes) allows, so registers
+// never limit it further.
+constexpr int row_min_blocks(int sigma) {
+    return sigma >= 13 ? 1 : (sigma == 12 ? 3 : (sigma == 11 ? 7 : (sigma == 10 ? 12 : 16)));
+}
+
 template <class A, int SIGMA>
-__global__ void __launch_bounds__((1 << SIGMA) / 16, (SIGMA >= 13 ? 1 : (SIGMA == 12 ? 3 : 2))) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
+__global__ void __launch_bounds__((1 << SIGMA) / 16, row_min_blocks(SIGMA)) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
     row_body<A, SIGMA>(d, blockIdx.x, m, tw);
 }
 
 template <class A, int C, int TL>
 __global__ void __launch_bounds__(COL_THREADS, 6) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
+    __shared__ uint2 top[16];  // the top three levels' twiddles (see ColInvArgs::top)
+    if (threadIdx.x < 16) {
+        const int e = threadIdx.x & 7;
+        top[threadIdx.x] = e == 0 ? make_uint2(0u, 0u) : __ldg((threadIdx.x < 8 ? tw.fwd : tw.inv) + e);
+    }
     const u32 words = (u32)C << TL;
+    tw.inv = stage_col_tw<TL>(smem, words, tw.inv);
     const int items = (int)(d.g.S / C);
     int it = blockIdx.x;
     if (it < items) coli_load<C>(d, it, smem);
@@ -59,14 +90,14 @@ __global__ void __launch_bounds__(COL_THREADS, 6) k_col_itft(const LargeDesc d, 
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        coli_compute_ct<A, C, TL>(d, it, smem + kb * words, m, tw);
+        coli_compute_ct<A, C, TL>(d, it, smem + kb * words, m, tw, top);
     }
 }
 
 // ------------------------------------------------------------ launchers
 template <class A, int C, int TL>
 static cudaError_t launch_colf_c(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
-    const size_t smem = (size_t)2 * ((size_t)C << TL) * sizeof(u32);
+    const size_t smem = col_smem_bytes<C, TL>();
     cudaError_t e = ensure_smem(k_col_fwd<A, C, TL>, COL_SMEM_MAX);
     if (e != cudaSuccess) return e;
     int grid = 0;
@@ -78,7 +109,7 @@ static cudaError_t launch_colf_c(const LargeDesc &d, ModParams m, TwTables tw, c
 
 template <class A, int C, int TL>
 static cudaError_t launch_coli_c(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
-    const size_t smem = (size_t)2 * ((size_t)C << TL) * sizeof(u32);
+    const size_t smem = col_smem_bytes<C, TL>();
     cudaError_t e = ensure_smem(k_col_itft<A, C, TL>, COL_SMEM_MAX);
     if (e != cudaSuccess) return e;
     int grid = 0;

@@ -38,11 +38,20 @@ __device__ __forceinline__ u32 shoup(u32 x, uint2 w, u32 p) {
 // [0, 2p) -> [0, p)
 __device__ __forceinline__ u32 canon2(u32 x, u32 p) { return umin32(x, x - p); }
 
+// 2p, computed by an opaque (but pure) instruction: the compiler then keeps
+// it in a register and folds "x - 2p, min" into one add-min instruction,
+// instead of re-deriving 2p from p at every use.
+__device__ __forceinline__ u32 twice(u32 p) {
+    u32 r;
+    asm("add.u32 %0, %1, %1;" : "=r"(r) : "r"(p));
+    return r;
+}
+
 template <bool LAZY>
 struct Arith {
     static constexpr bool lazy = LAZY;
     // The bound B (2p or p).
-    __device__ __forceinline__ static u32 bound(u32 p) { return LAZY ? 2u * p : p; }
+    __device__ __forceinline__ static u32 bound(u32 p) { return LAZY ? twice(p) : p; }
 
     // Merged Cooley-Tukey butterfly of one tree node with twiddle w:
     // (a, b) -> (a + w b, a - w b).  Inputs and outputs in [0, 2B).
@@ -84,8 +93,8 @@ struct Arith {
         const u32 p = m.p;
         // LAZY: both to [0, 2p) so a*b < 4p^2 < p*2^32.
         // !LAZY: a to [0, p), b in [0, 2p), so a*b < 2p^2 < p*2^32.
-        a = LAZY ? umin32(a, a - 2u * p) : canon2(a, p);
-        if (LAZY) b = umin32(b, b - 2u * p);
+        a = LAZY ? umin32(a, a - bound(p)) : canon2(a, p);
+        if (LAZY) b = umin32(b, b - bound(p));
         u32 lo = a * b;
         u32 hi = __umulhi(a, b);
         u32 q = lo * m.pinv;             // q*p = a*b mod 2^32

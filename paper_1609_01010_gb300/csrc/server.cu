@@ -2,12 +2,17 @@
 //
 // submit() queues a request and returns a ticket.  A scheduler thread admits
 // queued requests in arrival order while the bytes they hold (operands,
-// output and workspace) fit the memory budget, packs the admitted requests of
-// one prime into a work list and launches the persistent batched kernel on a
-// free stream.  Requests that arrive while launches are running are admitted
-// into the next launch on another stream as soon as budget and a stream are
-// free, so their work overlaps on the GPU.  A host callback enqueued after
-// each launch stamps its completion time; latency = completion - submit.
+// output and workspace) fit the memory budget, and hands the admitted
+// requests of one prime, as a group, to a free stream.  POLY_SERVE_BATCH
+// runs the group's small and medium requests (L <= 2^17) as one launch of
+// the persistent batched kernel whose work list holds them all, and its
+// large ones as plain products behind it; POLY_SERVE_PLAIN runs every
+// request as its own plain product (1 or 3 kernels) -- the
+// one-launch-per-product comparator.  Requests that arrive while launches
+// are running are admitted into the next group on another stream as soon as
+// budget and a stream are free, so their work overlaps on the GPU.  A host
+// callback enqueued after each group stamps its completion time; latency =
+// completion - submit.
 #include <stdint.h>
 #include <string.h>
 
@@ -34,6 +39,10 @@ static double now_us() {
 // Pinned staging per stream for one launch's work list (allocated at
 // creation: pinned allocations are not made while launches are in flight).
 constexpr size_t SRV_STAGE_BYTES = (size_t)32 << 20;
+// In POLY_SERVE_BATCH, requests with L above 2^SRV_BATCH_MAX_L fill the GPU
+// on their own: they run as plain products (the three-kernel path with its
+// tuned schedule) behind the group's batched launch.
+constexpr int SRV_BATCH_MAX_L = 17;
 
 struct SrvReq {
     uint64_t ticket;
@@ -73,6 +82,7 @@ using namespace pm;
 
 struct polymul_server {
     size_t budget = 0;
+    int mode = POLY_SERVE_BATCH;
     int dev = 0;
     std::vector<SrvStream> streams;
     std::mutex mu;
@@ -124,84 +134,121 @@ static size_t request_stage_bytes(int64_t n) {
     return sizeof(BatchDesc) + items * sizeof(WorkItem) + 2 * sizeof(int);
 }
 
+// Bytes a request holds while admitted: operands, output and the larger of
+// its batched and plain workspaces.
 static uint64_t request_bytes(int64_t za, int64_t zb) {
     const int64_t n = za + zb - 1;
     uint64_t bytes = (uint64_t)(za + zb + n) * 4;
     const int l = ceil_log2(n);
-    if (l > SMALL_MAX_LOG_L) bytes += (uint64_t)large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true) * 4;
+    if (l > SMALL_MAX_LOG_L)
+        bytes += (uint64_t)std::max(large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true),
+                                    large_workspace_words(n, l, schedule_for(l), true)) *
+                 4;
     return bytes;
 }
 
-// Packs `reqs` (one prime) into a work list and launches it on stream si.
-// Runs on the scheduler thread without the server lock.
+// Launches one admitted group (one prime) on stream si: the requests that
+// go through the batched kernel as one launch, the rest as plain products
+// behind it, then one completion callback for the group.  Runs on the
+// scheduler thread without the server lock.
 static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
     PrimeCtx *ctx = s->ctx[reqs[0].p];
     SrvStream &ss = s->streams[si];
-    const int64_t cnt = (int64_t)reqs.size();
-    std::vector<int64_t> za(cnt), zb(cnt);
-    std::vector<uint64_t> ao(cnt), bo(cnt), co(cnt);
-    int max_l = 0;
-    for (int64_t i = 0; i < cnt; ++i) {
-        za[i] = reqs[i].za;
-        zb[i] = reqs[i].zb;
-        ao[i] = (uint64_t)(uintptr_t)reqs[i].a;
-        bo[i] = (uint64_t)(uintptr_t)reqs[i].b;
-        co[i] = (uint64_t)(uintptr_t)reqs[i].c;
-        max_l = std::max(max_l, ceil_log2(reqs[i].n));
+    std::vector<SrvReq> batched, plain;
+    for (auto &r : reqs) {
+        if (s->mode == POLY_SERVE_PLAIN || ceil_log2(r.n) > SRV_BATCH_MAX_L) plain.push_back(r);
+        else batched.push_back(r);
     }
-    const int C = batch_tile_width(max_l);
-    std::vector<BatchDesc> descs;
-    std::vector<WorkItem> items;
-    uint64_t ws_bytes = 0;
-    size_t smem = 0;
-    int rc = build_worklist(ctx, cnt, za.data(), zb.data(), ao.data(), bo.data(), co.data(), C, descs, items,
-                            &ws_bytes, &smem);
-    if (rc) return rc;
-    const size_t d_bytes = descs.size() * sizeof(BatchDesc);
-    const size_t i_bytes = items.size() * sizeof(WorkItem);
-    const size_t c_bytes = (2 * cnt + 2) * sizeof(int);
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t stage = up(d_bytes) + up(i_bytes) + up(c_bytes);
-    const size_t total = stage + up(ws_bytes);
-    if (ss.pinned_bytes < stage + 256) return POLY_ENOMEM;  // admission keeps launches within the staging area
-    char *h = ss.pinned;
-    memcpy(h, descs.data(), d_bytes);
-    memcpy(h + up(d_bytes), items.data(), i_bytes);
-    memset(h + up(d_bytes) + up(i_bytes), 0, c_bytes);
-    char *dbuf = nullptr;
-    if (cudaMallocAsync((void **)&dbuf, total, ss.st) != cudaSuccess) return POLY_ENOMEM;
-    if (cudaMemcpyAsync(dbuf, h, stage, cudaMemcpyHostToDevice, ss.st) != cudaSuccess) return POLY_ECUDA;
-    BatchParams P;
-    P.a = nullptr;
-    P.b = nullptr;
-    P.c = nullptr;
-    P.ws = (u32 *)(dbuf + stage);
-    P.descs = (const BatchDesc *)dbuf;
-    P.items = (const WorkItem *)(dbuf + up(d_bytes));
-    P.nitems = (int)items.size();
-    P.counters = (int *)(dbuf + up(d_bytes) + up(i_bytes));
-    P.head = P.counters + 2 * cnt;
-    P.status = P.counters + 2 * cnt + 1;
-    P.m = ctx->m;
-    P.tw = ctx->tw;
-    P.spin_limit = BATCH_SPIN_LIMIT;
-    int grid = 0;
-    if (launch_batch(ctx->lazy, C, P, smem, &grid, ss.st) != cudaSuccess) return POLY_ECUDA;
     SrvLaunch *L = new SrvLaunch();
     L->srv = (void *)s;
     L->stream = si;
-    L->dbuf = dbuf;
-    L->status_dev = P.status;
+    if (!batched.empty()) {
+        const int64_t cnt = (int64_t)batched.size();
+        std::vector<int64_t> za(cnt), zb(cnt);
+        std::vector<uint64_t> ao(cnt), bo(cnt), co(cnt);
+        int max_l = 0;
+        for (int64_t i = 0; i < cnt; ++i) {
+            za[i] = batched[i].za;
+            zb[i] = batched[i].zb;
+            ao[i] = (uint64_t)(uintptr_t)batched[i].a;
+            bo[i] = (uint64_t)(uintptr_t)batched[i].b;
+            co[i] = (uint64_t)(uintptr_t)batched[i].c;
+            max_l = std::max(max_l, ceil_log2(batched[i].n));
+        }
+        const int C = batch_tile_width(max_l);
+        std::vector<BatchDesc> descs;
+        std::vector<WorkItem> items;
+        uint64_t ws_bytes = 0;
+        size_t smem = 0;
+        int rc = build_worklist(ctx, cnt, za.data(), zb.data(), ao.data(), bo.data(), co.data(), C, descs, items,
+                                &ws_bytes, &smem);
+        if (rc) {
+            delete L;
+            return rc;
+        }
+        const size_t d_bytes = descs.size() * sizeof(BatchDesc);
+        const size_t i_bytes = items.size() * sizeof(WorkItem);
+        const size_t c_bytes = (2 * cnt + 2) * sizeof(int);
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const size_t stage = up(d_bytes) + up(i_bytes) + up(c_bytes);
+        const size_t total = stage + up(ws_bytes);
+        if (ss.pinned_bytes < stage + 256) {  // admission keeps launches within the staging area
+            delete L;
+            return POLY_ENOMEM;
+        }
+        char *h = ss.pinned;
+        memcpy(h, descs.data(), d_bytes);
+        memcpy(h + up(d_bytes), items.data(), i_bytes);
+        memset(h + up(d_bytes) + up(i_bytes), 0, c_bytes);
+        char *dbuf = nullptr;
+        if (cudaMallocAsync((void **)&dbuf, total, ss.st) != cudaSuccess) {
+            delete L;
+            return POLY_ENOMEM;
+        }
+        L->dbuf = dbuf;
+        BatchParams P;
+        P.a = nullptr;
+        P.b = nullptr;
+        P.c = nullptr;
+        P.ws = (u32 *)(dbuf + stage);
+        P.descs = (const BatchDesc *)dbuf;
+        P.items = (const WorkItem *)(dbuf + up(d_bytes));
+        P.nitems = (int)items.size();
+        P.counters = (int *)(dbuf + up(d_bytes) + up(i_bytes));
+        P.head = P.counters + 2 * cnt;
+        P.status = P.counters + 2 * cnt + 1;
+        P.m = ctx->m;
+        P.tw = ctx->tw;
+        P.spin_limit = BATCH_SPIN_LIMIT;
+        int grid = 0;
+        // status word back to pinned host memory, behind the kernel on the stream
+        L->status_host = (int *)(h + stage);
+        if (cudaMemcpyAsync(dbuf, h, stage, cudaMemcpyHostToDevice, ss.st) != cudaSuccess ||
+            launch_batch(ctx->lazy, C, P, smem, &grid, ss.st) != cudaSuccess ||
+            cudaMemcpyAsync(L->status_host, P.status, sizeof(int), cudaMemcpyDeviceToHost, ss.st) != cudaSuccess) {
+            cudaFreeAsync(dbuf, ss.st);
+            delete L;
+            return POLY_ECUDA;
+        }
+    }
+    for (auto &r : plain) {
+        const int rc = run_product(r.p, 0, r.a, r.za, r.b, r.zb, r.c, ceil_log2(r.n), true, ss.st, nullptr);
+        if (rc) {
+            if (L->dbuf) cudaFreeAsync(L->dbuf, ss.st);
+            delete L;
+            return rc;
+        }
+    }
     for (auto &r : reqs) {
         L->tickets.push_back(r.ticket);
         L->t_submit.push_back(r.t_submit);
         L->bytes += r.bytes;
     }
-    // status word back to host memory (pinned, behind the kernel on the stream)
-    L->status_host = (int *)(h + stage);
-    if (cudaMemcpyAsync(L->status_host, P.status, sizeof(int), cudaMemcpyDeviceToHost, ss.st) != cudaSuccess)
+    if (cudaLaunchHostFunc(ss.st, srv_done_cb, L) != cudaSuccess) {
+        if (L->dbuf) cudaFreeAsync(L->dbuf, ss.st);
+        delete L;
         return POLY_ECUDA;
-    if (cudaLaunchHostFunc(ss.st, srv_done_cb, L) != cudaSuccess) return POLY_ECUDA;
+    }
     ss.busy = true;
     s->inflight.push_back(L);
     return POLY_OK;
@@ -223,7 +270,7 @@ static void srv_loop(polymul_server *s) {
                 ++i;
                 continue;
             }
-            const int st = *L->status_host;
+            const int st = L->status_host ? *L->status_host : POLY_OK;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 for (size_t j = 0; j < L->tickets.size(); ++j) {
@@ -234,7 +281,7 @@ static void srv_loop(polymul_server *s) {
                 s->in_use -= L->bytes;
             }
             s->cv.notify_all();
-            cudaFreeAsync(L->dbuf, s->streams[L->stream].st);
+            if (L->dbuf) cudaFreeAsync(L->dbuf, s->streams[L->stream].st);
             s->streams[L->stream].busy = false;
             delete L;
             s->inflight.erase(s->inflight.begin() + i);
@@ -296,12 +343,14 @@ static void srv_loop(polymul_server *s) {
 
 extern "C" {
 
-int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server **out) {
+int polymul_server_create(size_t mem_budget_bytes, int n_streams, int mode, polymul_server **out) {
     if (!out) return POLY_ENULL;
     *out = nullptr;
     if (mem_budget_bytes == 0 || n_streams < 1 || n_streams > 64) return POLY_EINVAL;
+    if (mode != POLY_SERVE_BATCH && mode != POLY_SERVE_PLAIN) return POLY_EINVAL;
     polymul_server *s = new polymul_server();
     s->budget = mem_budget_bytes;
+    s->mode = mode;
     if (cudaGetDevice(&s->dev) != cudaSuccess) {
         delete s;
         return POLY_ECUDA;
@@ -323,6 +372,11 @@ int polymul_server_create(size_t mem_budget_bytes, int n_streams, polymul_server
             for (int64_t k = 1; k <= ((int64_t)1 << logT); ++k) get_steps(c, (int64_t)1 << logT, k, &st, &ns);
         for (int t = SMALL_MAX_LOG_L + 1 - BATCH_SIGMA; t <= LARGE_MAX_LOG_T; ++t) {
             const int64_t T = (int64_t)1 << t;
+            for (int64_t k = T / 2 + 1; k <= T; ++k) get_steps(c, T, k, &st, &ns);
+        }
+        // and for the plain products' schedules
+        for (int l = SMALL_MAX_LOG_L + 1; l <= max_l; ++l) {
+            const int64_t T = (int64_t)1 << (l - schedule_for(l).sigma);
             for (int64_t k = T / 2 + 1; k <= T; ++k) get_steps(c, T, k, &st, &ns);
         }
     }

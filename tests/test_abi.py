@@ -55,5 +55,9 @@ def test_host_side_argument_checks(lib):
     h = ctypes.c_void_p()
     assert L.tft_plan_create(469762049, 0, 0, 5, ctypes.byref(h)) == POLY_EINVAL
     assert L.tft_plan_create(469762049, 0, 6, 5, ctypes.byref(h)) == POLY_EINVAL
+    srv = ctypes.c_void_p()
+    assert L.polymul_server_create(1 << 20, 4, 2, ctypes.byref(srv)) == POLY_EINVAL  # unknown mode
+    assert L.polymul_server_create(1 << 20, 0, 0, ctypes.byref(srv)) == POLY_EINVAL  # no stream
+    assert L.polymul_server_create(0, 4, 0, ctypes.byref(srv)) == POLY_EINVAL  # no budget
     assert L.polymul_strerror(-6).decode().startswith("a bounded wait")
     assert b"sm_103a" in L.polymul_version()

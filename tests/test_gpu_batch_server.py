@@ -121,12 +121,14 @@ def test_batch_bounded_wait_reports_timeout(gpu, kind):
                               alone(p, a[a_off[i]:a_off[i + 1]], b[b_off[i]:b_off[i + 1]], gpu))
 
 
-def test_server_mix_equals_alone_and_oracle(gpu, orc):
+@pytest.mark.parametrize("mode", [0, 1])  # batch, plain
+def test_server_mix_equals_alone_and_oracle(gpu, orc, mode):
     """Requests of mixed sizes and both primes submitted back to back (so they
-    are admitted while others run) give the same result as alone."""
+    are admitted while others run) give the same result as alone, in every
+    dispatch mode."""
     import torch
     from paper_1609_01010_gb300 import binding as B
-    rng = np.random.default_rng(9)
+    rng = np.random.default_rng(9 + mode)
     reqs = []
     for i in range(120):
         p = W.P1 if i % 2 else W.P2
@@ -137,7 +139,7 @@ def test_server_mix_equals_alone_and_oracle(gpu, orc):
         reqs.append((p, a, b, to_dev(a, gpu), to_dev(b, gpu),
                      torch.full((da + db + 1,), -1, dtype=torch.int32, device=gpu)))
     torch.cuda.synchronize()
-    srv = B.polymul_server_create(1 << 30, 4)
+    srv = B.polymul_server_create(1 << 30, 4, mode)
     try:
         tickets = [B.polymul_server_submit(srv, p, xa, len(a) - 1, xb, len(b) - 1, xc)
                    for p, a, b, xa, xb, xc in reqs]
