@@ -224,11 +224,19 @@ int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path);
 /* Load a table written by polymul_autotune. */
 int polymul_load_schedules(const char *json_path);
 
+/*
+ * The schedule the three-kernel path uses for L = 2^l (l in 14..24): row
+ * length 2^(*sigma) and column-tile width *C (autotuned or default).  The
+ * paper's counterpart is the DP search's chosen breakdown (Section 4).
+ * POLY_EINVAL outside that range, POLY_ENULL for null outputs.
+ */
+int polymul_get_schedule(int l, int *sigma, int *C);
+
 /* ---------------------------------------------------------------- serving */
 typedef struct polymul_server polymul_server;
 
 /* Dispatch modes of the server. */
-#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 as one persistent batched launch, larger ones plain */
+#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 as one persistent batched launch; large ones and lone requests plain */
 #define POLY_SERVE_PLAIN 1 /* every request as its own plain product (the comparator) */
 
 /*

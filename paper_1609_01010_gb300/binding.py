@@ -57,6 +57,7 @@ _SIGS = {
     "polymul_mod_batched_plain": (ctypes.c_int, [u32, i64, vp, I64P, vp, I64P, vp, I64P, vp]),
     "polymul_autotune": (ctypes.c_int, [u32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
     "polymul_load_schedules": (ctypes.c_int, [ctypes.c_char_p]),
+    "polymul_get_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
     "polymul_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
@@ -266,6 +267,13 @@ def polymul_load_schedules(json_path: str) -> None:
 
 
 # ------------------------------------------------------------ serving
+def polymul_get_schedule(l: int) -> tuple[int, int]:
+    """(sigma, C) of the three-kernel path for L = 2^l."""
+    sg, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().polymul_get_schedule(l, ctypes.byref(sg), ctypes.byref(c)), "polymul_get_schedule")
+    return sg.value, c.value
+
+
 SERVE_BATCH, SERVE_PLAIN = 0, 1
 
 

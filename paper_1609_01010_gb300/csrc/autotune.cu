@@ -133,4 +133,13 @@ int polymul_load_schedules(const char *json_path) {
     return loaded > 0 ? POLY_OK : POLY_EINVAL;
 }
 
+int polymul_get_schedule(int l, int *sigma, int *C) {
+    if (!sigma || !C) return POLY_ENULL;
+    if (l <= SMALL_MAX_LOG_L || l > POLY_MAX_LOG_L) return POLY_EINVAL;
+    const Schedule s = schedule_for(l);
+    *sigma = s.sigma;
+    *C = s.C;
+    return POLY_OK;
+}
+
 }  // extern "C"

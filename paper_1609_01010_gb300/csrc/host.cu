@@ -323,14 +323,15 @@ int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int
 static std::mutex g_sched_mu;
 static std::map<int, Schedule> g_sched;  // autotuned, by log2 L
 
+// Defaults from polymul_autotune runs on GB300 (both built-in primes agree
+// from l = 20 up; below that the three launches' latency dominates and the
+// candidates lie within about 1 us of each other).
 Schedule default_schedule(int l) {
-    Schedule s;
-    if (l <= 15) s.sigma = 10;
-    else if (l <= 20) s.sigma = 11;
-    else if (l <= 22) s.sigma = 12;
-    else s.sigma = 13;
-    s.C = 8;
-    return s;
+    if (l <= 15) return Schedule{10, 8};
+    if (l <= 19) return Schedule{11, 32};
+    if (l == 20) return Schedule{13, 32};
+    if (l <= 22) return Schedule{12, 8};
+    return Schedule{13, 8};
 }
 
 // Column tiles are double-buffered: 2 * T * C words must fit 128 KB.

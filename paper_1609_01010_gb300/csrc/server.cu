@@ -6,7 +6,9 @@
 // requests of one prime, as a group, to a free stream.  POLY_SERVE_BATCH
 // runs the group's small and medium requests (L <= 2^17) as one launch of
 // the persistent batched kernel whose work list holds them all, and its
-// large ones as plain products behind it; POLY_SERVE_PLAIN runs every
+// large ones -- or a lone request -- as plain products behind it (a work
+// list of one request only adds its build and upload to the latency);
+// POLY_SERVE_PLAIN runs every
 // request as its own plain product (1 or 3 kernels) -- the
 // one-launch-per-product comparator.  Requests that arrive while launches
 // are running are admitted into the next group on another stream as soon as
@@ -156,7 +158,7 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
     SrvStream &ss = s->streams[si];
     std::vector<SrvReq> batched, plain;
     for (auto &r : reqs) {
-        if (s->mode == POLY_SERVE_PLAIN || ceil_log2(r.n) > SRV_BATCH_MAX_L) plain.push_back(r);
+        if (s->mode == POLY_SERVE_PLAIN || reqs.size() == 1 || ceil_log2(r.n) > SRV_BATCH_MAX_L) plain.push_back(r);
         else batched.push_back(r);
     }
     SrvLaunch *L = new SrvLaunch();
