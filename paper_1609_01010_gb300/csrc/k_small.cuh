@@ -1,4 +1,5 @@
-// k_small.cu -- one CTA per product for transform lengths L <= 8192.
+// k_small.cu -- one CTA per product for transform lengths L <= 8192 (a
+// single product of L >= 1024 runs on a cluster instead: k_small_cl.cuh).
 //
 // The product is laid out as T = L/512 rows of 512 words in shared memory
 // (operands a and b side by side).  Steps, all in one launch:
@@ -14,6 +15,7 @@
 // L < 512 is computed as L = 512: the product does not depend on L.
 #pragma once
 #include "bodies.cuh"
+#include "k_small_cl.cuh"
 
 namespace pm {
 
@@ -24,9 +26,14 @@ __global__ void __launch_bounds__(32 << LOGT) k_small(const SmallDesc *__restric
     small_body<A, LOGT>(d, m, tw);
 }
 
+// A single product with T >= 2 rows runs on a cluster (k_small_cl.cuh);
+// descriptor arrays and T = 1 use one CTA per product.
 template <class A, int LOGT>
 static cudaError_t launch_small_t(const SmallDesc *d_desc, const SmallDesc &one, int count, ModParams m, TwTables tw,
                                   cudaStream_t st) {
+    if constexpr (LOGT >= 1) {
+        if (!d_desc && count == 1) return launch_small_cl_t<A, LOGT>(one, m, tw, st);
+    }
     constexpr int T = 1 << LOGT;
     const size_t smem = (size_t)2 * T * (1 << SMALL_LOG_S) * sizeof(u32);
     cudaError_t e = ensure_smem(k_small<A, LOGT>, smem);
