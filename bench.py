@@ -17,6 +17,9 @@ The same line also carries:
                zero-padded NTTs of 8192 and 16384 (Eq. (12));
   sweep        the large single products (d+1 in 2^16, 2^20, 2^22, 100000,
                1500000, 3000001): time, coeffs/s, compulsory-HBM fraction;
+  length_sweep the shape of the paper's Fig. 3: TFT product against the
+               power-of-two zero-padded NTT product for n in [2^14, 2^22],
+               eight lengths per octave;
   batched      4096 products (degrees log-uniform in [64, 65536]) in one
                persistent launch under a CUDA graph vs 4096 plain calls;
   serving      Poisson request stream into the continuous-batching server:
@@ -341,8 +344,44 @@ def tft_vs_padded(dev, stream, B):
             out[name + "_us"] = ev_time(f, 500, stream) * 1e3
     out["speedup_vs_padded_16384"] = out["padded_ntt_16384_us"] / out["tft_8192_us"]
     out["speedup_vs_padded_8192"] = out["padded_ntt_8192_us"] / out["tft_8192_us"]
-    out["note"] = "latency of one product per call (one CTA), CUDA events over 500 back-to-back calls"
+    out["note"] = ("latency of one product per call (L <= 8192: one cluster launch; 16384: three kernels), "
+                   "CUDA events over 500 back-to-back calls")
     return out
+
+
+def length_sweep(dev, stream, B, lo=14, hi=22, per_octave=8, reps=20):
+    """The shape of the paper's Fig. 3 (Section 5): TFT product time against
+    the power-of-two zero-padded NTT product (Eq. 12, padded to the next
+    power of two >= n) over lengths n in [2^lo, 2^hi] in fine steps; the NTT
+    is a staircase, the TFT follows n.  Equal operand lengths, n = 2z - 1."""
+    import torch
+    p = W.P1
+    zmax = (1 << hi) // 2 + 1
+    a = dev_u32(W.coeffs(W.SEED_BASE + 60, zmax, p), dev)
+    b = dev_u32(W.coeffs(W.SEED_BASE + 61, zmax, p), dev)
+    c = torch.empty(2 * zmax, dtype=torch.int32, device=dev)
+    sh = stream.cuda_stream
+    rows = []
+    with torch.cuda.stream(stream):
+        for e in range(lo * per_octave, hi * per_octave + 1):
+            n = int(round(2.0 ** (e / per_octave)))
+            z = (n + 1) // 2
+            n = 2 * z - 1
+            Lp = 1 << (n - 1).bit_length()
+            res = {"n": n, "L": Lp}
+            for name, pad in (("tft_us", None), ("padded_us", Lp)):
+                def f(i, pad=pad):
+                    if pad:
+                        B.polymul_mod_padded_async(p, a, z - 1, b, z - 1, c, pad, sh)
+                    else:
+                        B.polymul_mod_async(p, a, z - 1, b, z - 1, c, sh)
+                for i in range(3):
+                    f(i)
+                res[name] = ev_time(f, reps, stream) * 1e3
+            res["speedup"] = res["padded_us"] / res["tft_us"]
+            rows.append(res)
+    return {"p": p, "points": rows,
+            "note": "inputs L2-resident (one buffer set); padded = every butterfly of the power-of-two NTT"}
 
 
 def sweep(dev, stream, B, peaks, reps=20):
@@ -515,7 +554,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load before the timed region")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--skip", default="", help="comma list of parts to skip: e2e,cpu,padded,sweep,batched,serving")
+    ap.add_argument("--skip", default="",
+                    help="comma list of parts to skip: e2e,cpu,padded,sweep,fig3,batched,serving")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -592,6 +632,8 @@ def main():
             line["tft_vs_padded"] = tft_vs_padded(dev, stream, B)
         if "sweep" not in skip:
             line["sweep"] = sweep(dev, stream, B, peaks)
+        if "fig3" not in skip:
+            line["length_sweep"] = length_sweep(dev, stream, B)
         if "batched" not in skip:
             line["batched"] = batched(dev, stream, B)
         if "serving" not in skip and args.serve_seconds > 0:

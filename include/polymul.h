@@ -130,6 +130,26 @@ int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const u
 int polymul_profile_begin(void);
 int polymul_profile_end(double *ms4, int64_t *launches4);
 
+/*
+ * Cyclic convolution: c = a * b mod (x^N - 1), c_k = sum over i + j = k mod N
+ * of a_i b_j (Definition 4, Eq. 5), N >= 1 words in c.  a and b are given by
+ * their lengths za, zb (1 <= za, zb <= N), device buffers owned by the caller;
+ * coefficients in [0, p).  A power-of-two N >= 512 runs as Eq. 11 (transform
+ * of length N, pointwise product, inverse); any other N computes the linear
+ * product and folds it (a transient workspace of za + zb - 1 words from the
+ * stream-ordered pool).  POLY_EINVAL for lengths outside [1, N].
+ */
+int polymul_cyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32_t *b, int64_t zb, uint32_t *c,
+                         int64_t N, void *stream);
+
+/*
+ * Negacyclic convolution: c = a * b mod (x^N + 1) (x^N = -1), the second
+ * factor of Eq. 13's splitting of x^{2N} - 1.  Arguments as
+ * polymul_cyclic_async; computed as the linear product folded with a sign.
+ */
+int polymul_negacyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32_t *b, int64_t zb,
+                             uint32_t *c, int64_t N, void *stream);
+
 /* ---------------------------------------------------------------- TFT plans */
 typedef struct tft_plan tft_plan;
 

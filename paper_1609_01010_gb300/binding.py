@@ -57,6 +57,8 @@ _SIGS = {
     "polymul_mod_batched_plain": (ctypes.c_int, [u32, i64, vp, I64P, vp, I64P, vp, I64P, vp]),
     "polymul_autotune": (ctypes.c_int, [u32, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
     "polymul_load_schedules": (ctypes.c_int, [ctypes.c_char_p]),
+    "polymul_cyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
+    "polymul_negacyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_get_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -267,6 +269,18 @@ def polymul_load_schedules(json_path: str) -> None:
 
 
 # ------------------------------------------------------------ serving
+def polymul_cyclic_async(p: int, a, za: int, b, zb: int, c, N: int, stream=None) -> None:
+    """c (N words) = a * b mod (x^N - 1); za, zb are lengths (<= N)."""
+    _check(lib().polymul_cyclic_async(p, _ptr(a), za, _ptr(b), zb, _ptr(c), N, _stream(stream)),
+           "polymul_cyclic_async")
+
+
+def polymul_negacyclic_async(p: int, a, za: int, b, zb: int, c, N: int, stream=None) -> None:
+    """c (N words) = a * b mod (x^N + 1); za, zb are lengths (<= N)."""
+    _check(lib().polymul_negacyclic_async(p, _ptr(a), za, _ptr(b), zb, _ptr(c), N, _stream(stream)),
+           "polymul_negacyclic_async")
+
+
 def polymul_get_schedule(l: int) -> tuple[int, int]:
     """(sigma, C) of the three-kernel path for L = 2^l."""
     sg, c = ctypes.c_int(), ctypes.c_int()

@@ -412,11 +412,11 @@ static cudaEvent_t *prof_events(int kind) {
 // ------------------------------------------------------------ products
 // Fills a product descriptor for the small (one CTA) path.
 int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                  SmallDesc *d) {
+                  SmallDesc *d, int64_t n_out) {
     const int lp = l < SMALL_LOG_S ? SMALL_LOG_S : l;
     const int logT = lp - SMALL_LOG_S;
     const int64_t T = (int64_t)1 << logT, S = (int64_t)1 << SMALL_LOG_S;
-    const int64_t n = za + zb - 1;
+    const int64_t n = n_out < 0 ? za + zb - 1 : n_out;
     const int64_t k = prune ? (n + S - 1) / S : T;
     const ItftStep *st = nullptr;
     int ns = 0;
@@ -437,8 +437,8 @@ int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t
 }
 
 int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                  Schedule sch, LargeDesc *d) {
-    const int64_t n = za + zb - 1;
+                  Schedule sch, LargeDesc *d, int64_t n_out) {
+    const int64_t n = n_out < 0 ? za + zb - 1 : n_out;
     Geometry g = make_geometry(n, l, sch.sigma);
     if (!prune) g.k = g.T;
     const ItftStep *st = nullptr;
@@ -466,7 +466,7 @@ int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune) {
 }
 
 int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                cudaStream_t st, u32 *workspace) {
+                cudaStream_t st, u32 *workspace, int64_t n_out) {
     if (!a || !b || !c) return POLY_ENULL;
     PrimeCtx *ctx = nullptr;
     // Small products run with L padded to at least 512 (the product does not
@@ -477,7 +477,7 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     if (rc) return rc;
     if (small) {
         SmallDesc d;
-        rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d);
+        rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d, n_out);
         if (rc) return rc;
         cudaEvent_t *ev = prof_events(0);
         if (ev) cudaEventRecord(ev[0], st);
@@ -487,7 +487,7 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     }
     const Schedule sch = schedule_for(l);
     LargeDesc d;
-    rc = prepare_large(ctx, a, za, b, zb, c, l, prune, sch, &d);
+    rc = prepare_large(ctx, a, za, b, zb, c, l, prune, sch, &d, n_out);
     if (rc) return rc;
     const size_t bytes = (size_t)2 * d.g.k * d.g.S * sizeof(u32);
     u32 *ws = workspace;

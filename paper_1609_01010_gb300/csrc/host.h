@@ -55,12 +55,15 @@ std::map<int, Schedule> all_schedules();
 Geometry make_geometry(int64_t n, int l, int sigma);
 uint2 scale_const(u32 p, u64 scale);
 
+// n_out: the number of output coefficients; < 0 for the linear product's
+// za + zb - 1.  n_out = L (with za, zb <= L) gives the product mod x^L - 1
+// (the full transform, Eq. 11).
 int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                  SmallDesc *d);
+                  SmallDesc *d, int64_t n_out = -1);
 int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                  Schedule sch, LargeDesc *d);
+                  Schedule sch, LargeDesc *d, int64_t n_out = -1);
 int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune);
 int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                cudaStream_t st, u32 *workspace);
+                cudaStream_t st, u32 *workspace, int64_t n_out = -1);
 
 }  // namespace pm
