@@ -256,7 +256,7 @@ int polymul_get_schedule(int l, int *sigma, int *C);
 typedef struct polymul_server polymul_server;
 
 /* Dispatch modes of the server. */
-#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 as one persistent batched launch; large ones and lone requests plain */
+#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 (8 or more) as one persistent batched launch, the rest plain */
 #define POLY_SERVE_PLAIN 1 /* every request as its own plain product (the comparator) */
 
 /*

@@ -5,10 +5,10 @@
 // output and workspace) fit the memory budget, and hands the admitted
 // requests of one prime, as a group, to a free stream.  POLY_SERVE_BATCH
 // runs the group's small and medium requests (L <= 2^17) as one launch of
-// the persistent batched kernel whose work list holds them all, and its
-// large ones -- or a lone request -- as plain products behind it (a work
-// list of one request only adds its build and upload to the latency);
-// POLY_SERVE_PLAIN runs every
+// the persistent batched kernel whose work list holds them all -- when there
+// are at least SRV_BATCH_MIN of them -- and the rest as plain products behind
+// it (at light load a short work list only adds its build and upload to the
+// latency); POLY_SERVE_PLAIN runs every
 // request as its own plain product (1 or 3 kernels) -- the
 // one-launch-per-product comparator.  Requests that arrive while launches
 // are running are admitted into the next group on another stream as soon as
@@ -45,6 +45,10 @@ constexpr size_t SRV_STAGE_BYTES = (size_t)32 << 20;
 // on their own: they run as plain products (the three-kernel path with its
 // tuned schedule) behind the group's batched launch.
 constexpr int SRV_BATCH_MAX_L = 17;
+// ... and a group batches its small requests only when it has at least this
+// many: below that (light load) the work-list build and upload cost more
+// latency than the plain products' launches.
+constexpr size_t SRV_BATCH_MIN = 8;
 
 struct SrvReq {
     uint64_t ticket;
@@ -157,9 +161,12 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
     PrimeCtx *ctx = s->ctx[reqs[0].p];
     SrvStream &ss = s->streams[si];
     std::vector<SrvReq> batched, plain;
+    size_t small = 0;
+    for (auto &r : reqs) small += ceil_log2(r.n) <= SRV_BATCH_MAX_L;
+    const bool batch_small = s->mode == POLY_SERVE_BATCH && small >= SRV_BATCH_MIN;
     for (auto &r : reqs) {
-        if (s->mode == POLY_SERVE_PLAIN || reqs.size() == 1 || ceil_log2(r.n) > SRV_BATCH_MAX_L) plain.push_back(r);
-        else batched.push_back(r);
+        if (batch_small && ceil_log2(r.n) <= SRV_BATCH_MAX_L) batched.push_back(r);
+        else plain.push_back(r);
     }
     SrvLaunch *L = new SrvLaunch();
     L->srv = (void *)s;
