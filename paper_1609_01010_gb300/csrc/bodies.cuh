@@ -171,32 +171,34 @@ __device__ __noinline__ void colf_body(const LargeDesc d, int tile, int opnd, Mo
 
 // Row ib: remaining sigma levels of both operands, pointwise product,
 // unscaled inverse; result overwrites wa's row.  blockDim must be S/16.
-// Shared memory: 2*S words of data + (S-1) twiddles (8 bytes each).
+// Shared memory (row_smem_bytes): one exchange buffer of S words + the row's
+// S-1 twiddles (8 bytes each).  Pass 0 reads both rows from global memory
+// while the twiddles arrive by cp.async.
 template <class A, int SIGMA>
 __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     constexpr int S = 1 << SIGMA;
     constexpr int NP = RowPlan<SIGMA, 0>::NP;
-    u32 *ba = smem, *bb = smem + S;
-    uint2 *twb = reinterpret_cast<uint2 *>(smem + 2 * S);
+    u32 *buf = smem;
+    uint2 *twb = reinterpret_cast<uint2 *>(smem + S);
     const u32 tid = threadIdx.x;
     const u32 p = m.p;
     u32 *rowa = d.wa + (int64_t)ib * S;
-    stage_row<S>(ba, rowa);
-    stage_row<S>(bb, d.wb + (int64_t)ib * S);
     stage_tw<SIGMA>(twb, tw.fwd, d.g.t, ib);
-    cp_async_wait_all();
-    __syncthreads();
+    cp_async_commit();
     u32 xa[16], xb[16];
-    srow2_fwd<A, SIGMA, 0>(xa, xb, ba, bb, twb, tid, p);
+    srow2_load_g<SIGMA>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
+    cp_async_wait<0>();
+    __syncthreads();
+    srow2_fwd_1b<A, SIGMA, 0>(xa, xb, buf, twb, tid, p);
     const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
 #pragma unroll
     for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], cs, m);
-    __syncthreads();  // every thread is done with the forward twiddles
+    __syncthreads();  // every thread is done with the forward twiddles and buf
     stage_tw<SIGMA>(twb, tw.inv, d.g.t, ib);
     cp_async_wait_all();
     __syncthreads();
-    srow2_inv<A, SIGMA, NP - 1>(xa, ba, rowa, twb, tid, p);
+    srow2_inv<A, SIGMA, NP - 1>(xa, buf, rowa, twb, tid, p);
     __syncthreads();
 }
 

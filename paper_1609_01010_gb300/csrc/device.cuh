@@ -410,6 +410,49 @@ __device__ __forceinline__ void srow2_fwd(u32 *xa, u32 *xb, u32 *ba, u32 *bb, co
     }
 }
 
+// One operand's hand-over from forward pass P to pass P+1 through buf.
+template <int SIGMA, int P>
+__device__ __forceinline__ void row_xchg(u32 *x, u32 *buf, u32 tid) {
+    using RP = RowPlan<SIGMA, P>;
+    using RN = RowPlan<SIGMA, P + 1>;
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) st_con_s<RP::R>(buf, tid + g * RP::NT, x + (g << RP::R));
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < RN::NG; ++g) ld_str_s<RN::R, RN::S>(buf, tid + g * RN::NT, x + (g << RN::R));
+}
+
+// Forward passes of both operands through ONE exchange buffer: pass 0 starts
+// from the strided elements srow2_load_g read from global memory; between
+// passes operand a, then operand b, goes through `buf` (four barriers per
+// pass boundary instead of two, for half the shared memory).  The last pass
+// leaves the leaves in registers.
+template <int SIGMA>
+__device__ __forceinline__ void srow2_load_g(u32 *xa, u32 *xb, const u32 *ga, const u32 *gb, u32 tid) {
+    using RP = RowPlan<SIGMA, 0>;
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        ld_str_g<RP::R, RP::S>(ga, tid + g * RP::NT, xa + (g << RP::R));
+        ld_str_g<RP::R, RP::S>(gb, tid + g * RP::NT, xb + (g << RP::R));
+    }
+}
+
+template <class A, int SIGMA, int P>
+__device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, const uint2 *twb, u32 tid, u32 p) {
+    using RP = RowPlan<SIGMA, P>;
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
+        grp_fwd_s2_lvl<A, RP::R, RP::U0, 0>(xa + (g << RP::R), xb + (g << RP::R), twb, v, p);
+    }
+    if constexpr (P < RP::NP - 1) {
+        row_xchg<SIGMA, P>(xa, buf, tid);
+        row_xchg<SIGMA, P>(xb, buf, tid);
+        srow2_fwd_1b<A, SIGMA, P + 1>(xa, xb, buf, twb, tid, p);
+    }
+}
+
 // Inverse passes from the leaves in registers; the last pass (P = 0) writes
 // the row to global memory in natural order.
 template <class A, int SIGMA, int P>

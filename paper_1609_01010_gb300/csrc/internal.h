@@ -75,9 +75,9 @@ constexpr int LARGE_MAX_LOG_T = 10;
 // of T / 2^RELAX_LOG_T (see make_geometry).
 constexpr int RELAX_LOG_T = 3;
 
-// Shared memory of one row of the row stage: both operands' rows (2 S words)
+// Shared memory of one row of the row stage: one exchange buffer (S words)
 // and the row's twiddles (S entries of 8 bytes, entry 0 unused).
-inline size_t row_smem_bytes(int sigma) { return ((size_t)2 << sigma) * 4 + ((size_t)1 << sigma) * 8; }
+inline size_t row_smem_bytes(int sigma) { return ((size_t)1 << sigma) * 4 + ((size_t)1 << sigma) * 8; }
 
 struct Schedule {
     int sigma;  // row-block log size

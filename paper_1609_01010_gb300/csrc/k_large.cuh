@@ -16,7 +16,8 @@
 
 namespace pm {
 
-constexpr int COL_THREADS = 128;
+constexpr int COL_THREADS = 128;   // k_col_fwd
+constexpr int COLI_THREADS = 256;  // k_col_itft: more warps per tile for its mostly latency-bound passes
 // 2 * T * C * 4 bytes of tiles (at most 128 KB, schedule_valid's bound) and
 // up to 16 KB of column twiddles.
 constexpr size_t COL_SMEM_MAX = 144 * 1024;
@@ -59,10 +60,10 @@ __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, M
 }
 
 // Resident CTAs per SM the row kernel is compiled for: what its shared
-// memory (2 S words of rows + S twiddles of 8 bytes) allows, so registers
-// never limit it further.
+// memory (S words of exchange buffer + S twiddles of 8 bytes) allows, so
+// registers never limit it further.
 constexpr int row_min_blocks(int sigma) {
-    return sigma >= 13 ? 1 : (sigma == 12 ? 3 : (sigma == 11 ? 7 : (sigma == 10 ? 12 : 16)));
+    return sigma >= 13 ? 2 : (sigma == 12 ? 4 : (sigma == 11 ? 8 : 16));
 }
 
 template <class A, int SIGMA>
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__((1 << SIGMA) / 16, row_min_blocks(SIGMA)) k_ro
 }
 
 template <class A, int C, int TL>
-__global__ void __launch_bounds__(COL_THREADS, 6) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
+__global__ void __launch_bounds__(COLI_THREADS, 3) k_col_itft(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     __shared__ uint2 top[16];  // the top three levels' twiddles (see ColInvArgs::top)
     if (threadIdx.x < 16) {
@@ -113,9 +114,9 @@ static cudaError_t launch_coli_c(const LargeDesc &d, ModParams m, TwTables tw, c
     cudaError_t e = ensure_smem(k_col_itft<A, C, TL>, COL_SMEM_MAX);
     if (e != cudaSuccess) return e;
     int grid = 0;
-    e = persistent_grid((const void *)k_col_itft<A, C, TL>, COL_THREADS, smem, (int)(d.g.S / C), &grid);
+    e = persistent_grid((const void *)k_col_itft<A, C, TL>, COLI_THREADS, smem, (int)(d.g.S / C), &grid);
     if (e != cudaSuccess) return e;
-    k_col_itft<A, C, TL><<<grid, COL_THREADS, smem, st>>>(d, m, tw);
+    k_col_itft<A, C, TL><<<grid, COLI_THREADS, smem, st>>>(d, m, tw);
     return cudaGetLastError();
 }
 
