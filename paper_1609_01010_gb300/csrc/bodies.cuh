@@ -186,6 +186,7 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
     u32 *rowa = d.wa + (int64_t)ib * S;
     stage_tw<SIGMA>(twb, tw.fwd, d.g.t, ib);
     cp_async_commit();
+    pdl_wait();  // the rows come from the column-stage kernel
     u32 xa[16], xb[16];
     srow2_load_g<SIGMA>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
     cp_async_wait<0>();

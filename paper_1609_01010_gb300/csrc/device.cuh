@@ -81,6 +81,15 @@ __device__ __forceinline__ void grp_fwd_cp(u32 *x, const uint2 *__restrict__ tw,
     }
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// programmatic stream serialization may start while the previous kernel on
+// the stream still runs; pdl_wait() blocks until that kernel has completed
+// and its writes are visible.  The previous kernel lets it launch early with
+// pdl_launch_dependents().  Both are no-ops for kernels launched without the
+// attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // A twiddle pair from shared memory (the compile-time-shaped column kernels
 // stage the column tree's twiddles there once per CTA).
 __device__ __forceinline__ uint2 lds_tw(const uint2 *p) {

@@ -43,6 +43,7 @@ constexpr size_t col_smem_bytes() {
 template <class A, int C, int TL>
 __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
+    pdl_launch_dependents();  // the row kernel may start staging its twiddles
     const u32 words = (u32)C << TL;
     tw.fwd = stage_col_tw<TL>(smem, words, tw.fwd);
     const int items = 2 * (int)(d.g.S / C);  // (tile, operand) pairs
@@ -68,6 +69,7 @@ constexpr int row_min_blocks(int sigma) {
 
 template <class A, int SIGMA>
 __global__ void __launch_bounds__((1 << SIGMA) / 16, row_min_blocks(SIGMA)) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
+    pdl_launch_dependents();
     row_body<A, SIGMA>(d, blockIdx.x, m, tw);
 }
 
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(COLI_THREADS, 3) k_col_itft(const LargeDesc d,
     }
     const u32 words = (u32)C << TL;
     tw.inv = stage_col_tw<TL>(smem, words, tw.inv);
+    pdl_wait();  // the product rows come from the row kernel
     const int items = (int)(d.g.S / C);
     int it = blockIdx.x;
     if (it < items) coli_load<C>(d, it, smem);
@@ -96,6 +99,26 @@ __global__ void __launch_bounds__(COLI_THREADS, 3) k_col_itft(const LargeDesc d,
 }
 
 // ------------------------------------------------------------ launchers
+// Launch with programmatic stream serialization: the kernel may begin (and
+// run up to its pdl_wait) while the previous kernel on the stream finishes.
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kern)(Args...), int grid, int threads, size_t smem, cudaStream_t st,
+                              const LargeDesc &d, ModParams m, TwTables tw) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, d, m, tw);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <class A, int C, int TL>
 static cudaError_t launch_colf_c(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
     const size_t smem = col_smem_bytes<C, TL>();
@@ -116,8 +139,7 @@ static cudaError_t launch_coli_c(const LargeDesc &d, ModParams m, TwTables tw, c
     int grid = 0;
     e = persistent_grid((const void *)k_col_itft<A, C, TL>, COLI_THREADS, smem, (int)(d.g.S / C), &grid);
     if (e != cudaSuccess) return e;
-    k_col_itft<A, C, TL><<<grid, COLI_THREADS, smem, st>>>(d, m, tw);
-    return cudaGetLastError();
+    return launch_pdl(k_col_itft<A, C, TL>, grid, COLI_THREADS, smem, st, d, m, tw);
 }
 
 // t in 1..11 (schedule_valid); C in {8, 32, 128}.
@@ -148,8 +170,7 @@ static cudaError_t launch_rows(const LargeDesc &d, ModParams m, TwTables tw, cud
     const size_t smem = row_smem_bytes(SIGMA);
     cudaError_t e = ensure_smem(k_row_fused<A, SIGMA>, smem);
     if (e != cudaSuccess) return e;
-    k_row_fused<A, SIGMA><<<(int)d.g.k, S / 16, smem, st>>>(d, m, tw);
-    return cudaGetLastError();
+    return launch_pdl(k_row_fused<A, SIGMA>, (int)d.g.k, S / 16, smem, st, d, m, tw);
 }
 
 template <class A>
