@@ -5,7 +5,8 @@
 // (sigma, C) pair -- sigma sets where the tree is split between the column
 // and row stages (row length 2^sigma, radix-16 Stockham passes inside a row),
 // C the column-tile width -- is timed on a full-length product (n = L - 1)
-// with CUDA events; the fastest is kept and used by later plans.  The table
+// with CUDA events around back-to-back products; the fastest is kept and
+// used by later plans.  The table
 // is written as JSON:
 //   {"device": "...", "p": P, "schedules": [{"l": 20, "sigma": 11, "C": 16, "us": 12.3}, ...]}
 #include <stdio.h>
@@ -27,15 +28,21 @@ static float time_schedule(PrimeCtx *ctx, int l, Schedule sch, const u32 *a, con
     if (prepare_large(ctx, a, z, b, z, c, l, true, sch, &d)) return -1.f;
     d.wa = ws;
     d.wb = ws + d.g.k * d.g.S;
-    std::vector<float> t;
-    for (int it = 0; it < 8; ++it) {
-        cudaEventRecord(e0, st);
+    // back-to-back products, as a stream of calls runs them (the row and
+    // column-ITFT kernels overlap the previous kernel's tail)
+    constexpr int reps = 16;
+    for (int it = 0; it < 4; ++it)
         if (launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st) != cudaSuccess) return -1.f;
+    std::vector<float> t;
+    for (int rnd = 0; rnd < 5; ++rnd) {
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < reps; ++it)
+            if (launch_large(ctx->lazy, d, sch, ctx->m, ctx->tw, st) != cudaSuccess) return -1.f;
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (it >= 2) t.push_back(ms);
+        t.push_back(ms / reps);
     }
     std::sort(t.begin(), t.end());
     return t[t.size() / 2] * 1000.f;

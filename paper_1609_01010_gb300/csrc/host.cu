@@ -323,15 +323,23 @@ int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int
 static std::mutex g_sched_mu;
 static std::map<int, Schedule> g_sched;  // autotuned, by log2 L
 
-// Defaults from polymul_autotune runs on GB300 (both built-in primes agree
-// from l = 20 up; below that the three launches' latency dominates and the
-// candidates lie within about 1 us of each other).
+// Defaults from timing every valid (sigma, C) on GB300 with back-to-back
+// products (polymul_autotune measures the same way); the row kernel and the
+// column ITFT start early under programmatic dependent launch, so the best
+// split differs from one that isolated launches would pick.
 Schedule default_schedule(int l) {
-    if (l <= 15) return Schedule{10, 8};
-    if (l <= 19) return Schedule{11, 32};
-    if (l == 20) return Schedule{13, 32};
-    if (l <= 22) return Schedule{12, 8};
-    return Schedule{13, 8};
+    switch (l) {
+        case 14: return Schedule{11, 128};
+        case 15: return Schedule{9, 8};
+        case 16:
+        case 17: return Schedule{10, 32};
+        case 18: return Schedule{11, 32};
+        case 19: return Schedule{12, 32};
+        case 20: return Schedule{11, 8};
+        case 21:
+        case 22: return Schedule{12, 8};
+        default: return l < 14 ? Schedule{10, 8} : Schedule{13, 8};
+    }
 }
 
 // Column tiles are double-buffered: 2 * T * C words must fit 128 KB.
