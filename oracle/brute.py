@@ -4,6 +4,8 @@ Each function computes its result by a route other than the oracle's:
  - ``kronecker_product``: the polynomial product through Python's big-integer
    multiplication (Kronecker substitution), then reduced mod p.  It is the
    product of Definition 2 / Eq. (2) computed by an independent library routine.
+ - ``kronecker_int_product``: the same product over the integers (no reduction),
+   for the exact integer product of the three primes algorithm (Section 1).
  - ``horner``: evaluation of a polynomial at a point.
  - ``direct_tft``: the TFT outputs by definition, g(w^{rev_l(i)}) for i < n
    (Section 3; van der Hoeven's bit-reversed order), each by Horner.
@@ -31,6 +33,29 @@ def kronecker_product(a, b, p: int) -> list[int]:
     out = []
     for _ in range(n):
         out.append((C & mask) % p)
+        C >>= bits
+    return out
+
+
+def kronecker_int_product(a, b) -> list[int]:
+    """(sum a_i x^i)(sum b_j x^j) over the integers, via one big-integer
+    multiplication; coefficients must be non-negative."""
+    a = [int(v) for v in a]
+    b = [int(v) for v in b]
+    n = len(a) + len(b) - 1
+    top = max(a) * max(b) * min(len(a), len(b))
+    bits = max(top.bit_length(), 1) + 1
+    A = 0
+    for v in reversed(a):
+        A = (A << bits) | v
+    B = 0
+    for v in reversed(b):
+        B = (B << bits) | v
+    C = A * B
+    mask = (1 << bits) - 1
+    out = []
+    for _ in range(n):
+        out.append(C & mask)
         C >>= bits
     return out
 

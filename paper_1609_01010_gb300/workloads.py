@@ -18,7 +18,9 @@ Workloads (seeds 0x16090000 + k for workload k):
   4. 4096 independent products mod 2013265921, each operand degree
      log-uniform in [64, 65536];
   5. a Poisson request stream (20 000 req/s) of products mod 469762049 or
-     2013265921 (fair coin), degrees log-uniform in [256, 2^20].
+     2013265921 (fair coin), degrees log-uniform in [256, 2^20];
+  6. exact integer products (the three primes algorithm): two operands of
+     equal length z with coefficients uniform over all 32-bit words.
 """
 from __future__ import annotations
 
@@ -52,6 +54,11 @@ def coeffs(seed: int, count: int, p: int) -> np.ndarray:
     x = splitmix64(seed, count) >> np.uint64(32)
     with np.errstate(over="ignore"):
         return ((x * np.uint64(p)) >> np.uint64(32)).astype(np.uint32)
+
+
+def words(seed: int, count: int) -> np.ndarray:
+    """`count` values uniform in [0, 2^32) as uint32 (the top half of each output)."""
+    return (splitmix64(seed, count) >> np.uint64(32)).astype(np.uint32)
 
 
 def subseed(seed: int, i: int) -> int:
@@ -92,6 +99,13 @@ def workload3(z: int):
     """(p, a, b): equal operand lengths z (degree z-1) mod 469762049."""
     a, b = operands(subseed(SEED_BASE + 3, z), z - 1, z - 1, P1)
     return P1, a, b
+
+
+def workload6(z: int, zb: int | None = None):
+    """(a, b): operands of lengths z and zb (default z), uniform 32-bit coefficients."""
+    zb = z if zb is None else zb
+    s = subseed(SEED_BASE + 6, z * 7919 + zb)
+    return words(s + 1, z), words(s + 2, zb)
 
 
 def batch_degrees(count: int = 4096, lo: int = 64, hi: int = 65536, seed: int = SEED_BASE + 4):
