@@ -17,6 +17,9 @@ The same line also carries:
                zero-padded NTTs of 8192 and 16384 (Eq. (12));
   sweep        the large single products (d+1 in 2^16, 2^20, 2^22, 100000,
                1500000, 3000001): time, coeffs/s, compulsory-HBM fraction;
+  crt3         exact integer products of 32-bit-coefficient operands (three
+               primes and the CRT, Section 1) at z = 2^16, 2^20, 3000001,
+               against three modular products of the same size;
   length_sweep the shape of the paper's Fig. 3: TFT product against the
                power-of-two zero-padded NTT product for n in [2^14, 2^22],
                eight lengths per octave;
@@ -414,6 +417,51 @@ def sweep(dev, stream, B, peaks, reps=20):
     return rows
 
 
+def exact_coeff(a, b, k):
+    """c_k = sum a_i b_{k-i} over the integers (uint64 halves summed apart)."""
+    lo = max(0, k - (len(b) - 1))
+    hi = min(k, len(a) - 1)
+    pr = a[lo:hi + 1].astype(np.uint64) * b[k - hi:k - lo + 1][::-1].astype(np.uint64)
+    return (int(np.sum(pr >> np.uint64(32), dtype=np.uint64)) << 32) + int(np.sum(pr & np.uint64(0xFFFFFFFF),
+                                                                                   dtype=np.uint64))
+
+
+def crt3(dev, stream, B, mod_us, reps=20):
+    """Exact integer products (three primes + CRT) of two operands of z
+    uniform 32-bit words, against three modular products of the same size."""
+    import torch
+    rows = []
+    for z in (1 << 16, 1 << 20, 3000001):
+        a, b = W.workload6(z)
+        n = 2 * z - 1
+        sets = max(2, min(8, int(2 * L2_BYTES / (28 * z)) + 1))
+        A = [dev_u32(a, dev) for _ in range(sets)]
+        Bv = [dev_u32(b, dev) for _ in range(sets)]
+        C = [torch.empty((n, 3), dtype=torch.int32, device=dev) for _ in range(sets)]
+        sh = stream.cuda_stream
+
+        def f(i):
+            j = i % sets
+            B.polymul_crt3_async(A[j], z - 1, Bv[j], z - 1, C[j], sh)
+        with torch.cuda.stream(stream):
+            for i in range(3):
+                f(i)
+            ms = ev_time(f, reps, stream)
+        got = C[(reps - 1) % sets].cpu().numpy().view(np.uint32)
+        ks = [0, n // 2, n - 1] + [int(k) for k in np.random.default_rng(z).integers(0, n, 13)]
+        ok = all(int(got[k, 0]) + (int(got[k, 1]) << 32) + (int(got[k, 2]) << 64) == exact_coeff(a, b, k)
+                 for k in ks)
+        byt = 4 * 2 * z + 12 * n
+        row = {"z": z, "n": n, "us": ms * 1e3, "coeffs_per_s": n / (ms * 1e-3),
+               "hbm_compulsory_gbs": byt / (ms * 1e-3) / 1e9, "correct_sampled": ok}
+        if z in mod_us:
+            row["vs_three_mod_products"] = 3 * mod_us[z] / (ms * 1e3)
+        rows.append(row)
+        del A, Bv, C
+        torch.cuda.empty_cache()
+    return rows
+
+
 def batched(dev, stream, B, reps=5):
     import torch
     p, a, a_off, b, b_off, c_off = W.workload4()
@@ -555,7 +603,7 @@ def main():
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load before the timed region")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--skip", default="",
-                    help="comma list of parts to skip: e2e,cpu,padded,sweep,fig3,batched,serving")
+                    help="comma list of parts to skip: e2e,cpu,padded,sweep,crt3,fig3,batched,serving")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -632,6 +680,9 @@ def main():
             line["tft_vs_padded"] = tft_vs_padded(dev, stream, B)
         if "sweep" not in skip:
             line["sweep"] = sweep(dev, stream, B, peaks)
+        if "crt3" not in skip:
+            mod_us = {r["z"]: r["us"] for r in line.get("sweep", [])}
+            line["crt3"] = crt3(dev, stream, B, mod_us)
         if "fig3" not in skip:
             line["length_sweep"] = length_sweep(dev, stream, B)
         if "batched" not in skip:

@@ -150,6 +150,24 @@ int polymul_cyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32
 int polymul_negacyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32_t *b, int64_t zb,
                              uint32_t *c, int64_t N, void *stream);
 
+/*
+ * Exact integer product of two polynomials with unsigned 32-bit coefficients,
+ * by the three primes algorithm that Section 1 names as the route from
+ * modular polynomial multiplication to multiplication over the integers:
+ * the product modulo q0 = 469762049, q1 = 2013265921 and q2 = 754974721
+ * (three TFT products, Eq. 14), recombined by the Chinese remainder theorem
+ * (Garner's mixed-radix form).
+ *   a: device, da+1 words, any value in [0, 2^32); b likewise (db+1 words).
+ *   c: device, 3*(da+db+1) words: coefficient k of a*b over the integers is
+ *      c[3k] + 2^32 c[3k+1] + 2^64 c[3k+2] (little-endian 32-bit words).
+ * Exact for n = da+db+1 <= 2^24: every coefficient is below
+ * min(da+1, db+1) (2^32-1)^2 < 2^87 < q0 q1 q2 (about 2^89.2).
+ * POLY_ETOO_LONG beyond 2^24, POLY_EINVAL for negative degrees, POLY_ENULL for
+ * null pointers.  Workspace: 3 (da+db+2) + 3 n words from the stream-ordered
+ * pool, released on `stream`; the three products also take their own.
+ */
+int polymul_crt3_async(const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c, void *stream);
+
 /* ---------------------------------------------------------------- TFT plans */
 typedef struct tft_plan tft_plan;
 

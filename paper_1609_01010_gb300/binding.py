@@ -59,6 +59,7 @@ _SIGS = {
     "polymul_load_schedules": (ctypes.c_int, [ctypes.c_char_p]),
     "polymul_cyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_negacyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
+    "polymul_crt3_async": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
     "polymul_get_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -279,6 +280,12 @@ def polymul_negacyclic_async(p: int, a, za: int, b, zb: int, c, N: int, stream=N
     """c (N words) = a * b mod (x^N + 1); za, zb are lengths (<= N)."""
     _check(lib().polymul_negacyclic_async(p, _ptr(a), za, _ptr(b), zb, _ptr(c), N, _stream(stream)),
            "polymul_negacyclic_async")
+
+
+def polymul_crt3_async(a, da: int, b, db: int, c, stream=None) -> None:
+    """c (3*(da+db+1) words) = a * b over the integers, 32-bit coefficients in,
+    96-bit little-endian coefficients out (three primes and the CRT)."""
+    _check(lib().polymul_crt3_async(_ptr(a), da, _ptr(b), db, _ptr(c), _stream(stream)), "polymul_crt3_async")
 
 
 def polymul_get_schedule(l: int) -> tuple[int, int]:

@@ -52,6 +52,10 @@ def test_host_side_argument_checks(lib):
     assert L.polymul_mod_async(469762049, 16, -1, 16, 3, 16, None) == POLY_EINVAL
     assert L.polymul_mod_padded_async(469762049, 16, 3, 16, 3, 16, 6, None) == POLY_EINVAL  # Lp not a power of 2
     assert L.polymul_mod_padded_async(469762049, 16, 3, 16, 3, 16, 4, None) == POLY_EINVAL  # Lp < n
+    # exact integer product: checks precede any CUDA call
+    assert L.polymul_crt3_async(None, 3, 16, 3, 16, None) == POLY_ENULL
+    assert L.polymul_crt3_async(16, 3, 16, -2, 16, None) == POLY_EINVAL
+    assert L.polymul_crt3_async(16, 1 << 23, 16, 1 << 23, 16, None) == -2  # n = 2^24 + 1: POLY_ETOO_LONG
     h = ctypes.c_void_p()
     assert L.tft_plan_create(469762049, 0, 0, 5, ctypes.byref(h)) == POLY_EINVAL
     assert L.tft_plan_create(469762049, 0, 6, 5, ctypes.byref(h)) == POLY_EINVAL
