@@ -171,35 +171,52 @@ __device__ __noinline__ void colf_body(const LargeDesc d, int tile, int opnd, Mo
 
 // Row ib: remaining sigma levels of both operands, pointwise product,
 // unscaled inverse; result overwrites wa's row.  blockDim must be S/16.
-// Shared memory (row_smem_bytes): one exchange buffer of S words + the row's
-// S-1 twiddles (8 bytes each).  Pass 0 reads both rows from global memory
-// while the twiddles arrive by cp.async.
+// Shared memory (row_smem_bytes): one exchange buffer of S words, the row's
+// S-1 forward twiddles (8 bytes each) and, for sigma <= 12, the inverse
+// twiddles of the sub-levels before the last pass (2^8 entries).  Pass 0
+// reads both rows from global memory while the twiddles arrive by cp.async;
+// the last pass's inverse twiddles are fetched during the forward passes
+// (srow2_fwd_1b, EARLY), so the inverse starts without a staging wait.  For
+// sigma = 13 (whose shared inverse levels would take 32 KB) the inverse
+// table is staged over the forward one after the pointwise product.
 template <class A, int SIGMA>
 __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     constexpr int S = 1 << SIGMA;
     constexpr int NP = RowPlan<SIGMA, 0>::NP;
+    constexpr int UL = row_last_u0<SIGMA>();
+    constexpr bool EARLY = SIGMA <= 12;
     u32 *buf = smem;
     uint2 *twb = reinterpret_cast<uint2 *>(smem + S);
+    uint2 *twlo = twb + S;  // EARLY: inverse sub-levels < UL
     const u32 tid = threadIdx.x;
     const u32 p = m.p;
+    const int t = d.g.t;
     u32 *rowa = d.wa + (int64_t)ib * S;
-    stage_tw<SIGMA>(twb, tw.fwd, d.g.t, ib);
+    stage_tw<SIGMA>(twb, tw.fwd, t, ib);
+    if constexpr (EARLY) stage_tw<UL>(twlo, tw.inv, t, ib);
     cp_async_commit();
     pdl_wait();  // the rows come from the column-stage kernel
     u32 xa[16], xb[16];
     srow2_load_g<SIGMA>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
     cp_async_wait<0>();
     __syncthreads();
-    srow2_fwd_1b<A, SIGMA, 0>(xa, xb, buf, twb, tid, p);
+    srow2_fwd_1b<A, SIGMA, 0, EARLY>(xa, xb, buf, twb, tid, p, tw.inv, t, ib);
     const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
 #pragma unroll
     for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], cs, m);
-    __syncthreads();  // every thread is done with the forward twiddles and buf
-    stage_tw<SIGMA>(twb, tw.inv, d.g.t, ib);
-    cp_async_wait_all();
-    __syncthreads();
-    srow2_inv<A, SIGMA, NP - 1>(xa, buf, rowa, twb, tid, p);
+    RowTw rt;
+    if constexpr (EARLY) {
+        cp_async_wait_all();  // this thread's own last-pass inverse twiddles
+        rt = RowTw{twlo, twb, reinterpret_cast<const uint2 *>(buf)};
+    } else {
+        __syncthreads();  // every thread is done with the forward twiddles and buf
+        stage_tw<SIGMA>(twb, tw.inv, t, ib);
+        cp_async_wait_all();
+        __syncthreads();
+        rt = RowTw{twb, twb, twb + (S >> 1)};
+    }
+    srow2_inv<A, SIGMA, NP - 1>(xa, buf, rowa, rt, tid, p);
     __syncthreads();
 }
 

@@ -310,11 +310,12 @@ __device__ __forceinline__ void stage_row(u32 *buf, const u32 *g) {
     for (u32 ch = threadIdx.x; ch < S / 4; ch += blockDim.x) cp_async16(buf + swz(4 * ch), g + 4 * ch);
 }
 
-// Copies the S-1 twiddles of row ib's subtree (depth t) from the global
-// table into twb (entries [2^u, 2^(u+1)) for sub-level u).
-template <int SIGMA>
+// Copies the twiddles of sub-levels u < LEVELS of row ib's subtree (depth t)
+// from the global table into twb (entries [2^u, 2^(u+1)) for sub-level u);
+// LEVELS = sigma gives all S-1 of them.
+template <int LEVELS>
 __device__ __forceinline__ void stage_tw(uint2 *twb, const uint2 *__restrict__ tab, int t, u32 ib) {
-    constexpr u32 S = 1u << SIGMA;
+    constexpr u32 S = 1u << LEVELS;
     if (threadIdx.x == 0) cp_async8(twb + 1, tab + tw_index(t, ib));  // level 0: one entry
     // levels u >= 1: chunk x (two entries) belongs to level u with x + 1 in [2^(u-1), 2^u)
     for (u32 x = threadIdx.x; x < S / 2 - 1; x += blockDim.x) {
@@ -383,6 +384,73 @@ __device__ __forceinline__ void grp_inv_s_lvl(u32 *x, const uint2 *twb, u32 v, u
         grp_inv_s_lvl<A, R, U0, D - 1>(x, twb, v, p);
     }
 }
+// Where the row stage's inverse twiddles live.  Sub-level u's entry 2^u + j
+// is lo[2^u + j] for u < UL (the levels every thread reads), mid[2^u + j]
+// for UL <= u < sigma - 1, and top[j] for u = sigma - 1, where UL is the
+// first sub-level of the last pass.  The last pass's entries are private to
+// one thread each (see row_body).
+struct RowTw {
+    const uint2 *lo, *mid, *top;
+};
+template <int SIGMA>
+__host__ __device__ constexpr int row_last_u0() {
+    return 4 * (RowPlan<SIGMA, 0>::NP - 1);
+}
+template <int SIGMA, int LEV>
+__device__ __forceinline__ const uint2 *rt_level(const RowTw &t) {
+    if constexpr (LEV == SIGMA - 1) return t.top;
+    else if constexpr (LEV >= row_last_u0<SIGMA>()) return t.mid + (1u << LEV);
+    else return t.lo + (1u << LEV);
+}
+template <class A, int SIGMA, int R, int U0, int D>
+__device__ __forceinline__ void grp_inv_rt_lvl(u32 *x, const RowTw &rt, u32 v, u32 p) {
+    if constexpr (D >= 0) {
+        constexpr int half = 1 << (R - 1 - D);
+        uint2 w[1 << D];
+        ld_tw_level<D>(w, rt_level<SIGMA, U0 + D>(rt), v);
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e)
+#pragma unroll
+            for (int jj = 0; jj < half; ++jj) A::gs(x[e * 2 * half + jj], x[e * 2 * half + jj + half], w[e], p);
+        grp_inv_rt_lvl<A, SIGMA, R, U0, D - 1>(x, rt, v, p);
+    }
+}
+
+// Copies of one thread's inverse twiddles for the last pass (groups
+// v = tid + g*NT): sub-level sigma-1 into top (entry 2^(sigma-1) + j at top[j]),
+// the pass's other levels (MID) into twb at their usual entries.
+template <int SIGMA, bool MID>
+__device__ __forceinline__ void row_last_inv_tw(uint2 *dst, const uint2 *__restrict__ itab, int t, u32 ib, u32 tid) {
+    using RP = RowPlan<SIGMA, RowPlan<SIGMA, 0>::NP - 1>;
+    constexpr int U0 = RP::U0, R = RP::R;
+#pragma unroll
+    for (int g = 0; g < RP::NG; ++g) {
+        const u32 v = tid + g * RP::NT;
+        if constexpr (!MID) {
+            constexpr int D = R - 1;
+            const uint2 *src = itab + tw_index(t + U0 + D, (ib << (U0 + D)) + (v << D));
+            if constexpr (D == 0) {
+                cp_async8(dst + v, src);
+            } else {
+#pragma unroll
+                for (int e = 0; e < (1 << D); e += 2) cp_async16(dst + (v << D) + e, src + e);
+            }
+        } else {
+#pragma unroll
+            for (int D = 0; D < R - 1; ++D) {
+                const uint2 *src = itab + tw_index(t + U0 + D, (ib << (U0 + D)) + (v << D));
+                uint2 *d2 = dst + (1u << (U0 + D)) + (v << D);
+                if (D == 0) {
+                    cp_async8(d2, src);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < (1 << D); e += 2) cp_async16(d2 + e, src + e);
+                }
+            }
+        }
+    }
+}
+
 template <class A, int R, int U0>
 __device__ __forceinline__ void grp_fwd_s(u32 *x, const uint2 *twb, u32 v, u32 p) {
     grp_fwd_s_lvl<A, R, U0, 0>(x, twb, v, p);
@@ -447,9 +515,22 @@ __device__ __forceinline__ void srow2_load_g(u32 *xa, u32 *xb, const u32 *ga, co
     }
 }
 
-template <class A, int SIGMA, int P>
-__device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, const uint2 *twb, u32 tid, u32 p) {
+//
+// EARLY: the inverse twiddles of the last pass are fetched while the forward
+// runs.  Its groups' twiddles are private to their thread, so before the
+// last forward pass (once every thread has read `buf`) each thread starts
+// the copy of its sub-level sigma-1 inverse twiddles into `buf` (exactly S
+// words), and right after the pass (its forward twiddles consumed) the copy
+// of its other inverse twiddles of that pass over the forward ones in twb.
+template <class A, int SIGMA, int P, bool EARLY>
+__device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, uint2 *twb, u32 tid, u32 p,
+                                             const uint2 *__restrict__ itab, int t, u32 ib) {
     using RP = RowPlan<SIGMA, P>;
+    if constexpr (EARLY && P == RP::NP - 1) {
+        __syncthreads();  // every thread has loaded its elements from buf
+        row_last_inv_tw<SIGMA, false>(reinterpret_cast<uint2 *>(buf), itab, t, ib, tid);
+        cp_async_commit();
+    }
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
@@ -458,14 +539,17 @@ __device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, const u
     if constexpr (P < RP::NP - 1) {
         row_xchg<SIGMA, P>(xa, buf, tid);
         row_xchg<SIGMA, P>(xb, buf, tid);
-        srow2_fwd_1b<A, SIGMA, P + 1>(xa, xb, buf, twb, tid, p);
+        srow2_fwd_1b<A, SIGMA, P + 1, EARLY>(xa, xb, buf, twb, tid, p, itab, t, ib);
+    } else if constexpr (EARLY) {
+        row_last_inv_tw<SIGMA, true>(twb, itab, t, ib, tid);
+        cp_async_commit();
     }
 }
 
 // Inverse passes from the leaves in registers; the last pass (P = 0) writes
 // the row to global memory in natural order.
 template <class A, int SIGMA, int P>
-__device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const uint2 *twb, u32 tid, u32 p) {
+__device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const RowTw &rt, u32 tid, u32 p) {
     using RP = RowPlan<SIGMA, P>;
     if constexpr (P < RP::NP - 1) {
 #pragma unroll
@@ -474,7 +558,7 @@ __device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const uint
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
-        grp_inv_s<A, RP::R, RP::U0>(x + (g << RP::R), twb, v, p);
+        grp_inv_rt_lvl<A, SIGMA, RP::R, RP::U0, RP::R - 1>(x + (g << RP::R), rt, v, p);
     }
     if constexpr (P == 0) {
 #pragma unroll
@@ -484,7 +568,7 @@ __device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const uint
 #pragma unroll
         for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(ba, tid + g * RP::NT, x + (g << RP::R));
         __syncthreads();
-        srow2_inv<A, SIGMA, P - 1>(x, ba, gdst, twb, tid, p);
+        srow2_inv<A, SIGMA, P - 1>(x, ba, gdst, rt, tid, p);
     }
 }
 
