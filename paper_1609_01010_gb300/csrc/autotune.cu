@@ -51,7 +51,7 @@ static float time_schedule(PrimeCtx *ctx, int l, Schedule sch, const u32 *a, con
 extern "C" {
 
 int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path) {
-    if (lo_log < SMALL_MAX_LOG_L + 1) lo_log = SMALL_MAX_LOG_L + 1;
+    if (lo_log < SINGLE_SMALL_MAX_LOG_L + 1) lo_log = SINGLE_SMALL_MAX_LOG_L + 1;
     if (hi_log > POLY_MAX_LOG_L || hi_log < lo_log) return POLY_EINVAL;
     PrimeCtx *ctx = nullptr;
     int rc = get_prime(p, 0, hi_log, &ctx, nullptr);
@@ -142,7 +142,7 @@ int polymul_load_schedules(const char *json_path) {
 
 int polymul_get_schedule(int l, int *sigma, int *C) {
     if (!sigma || !C) return POLY_ENULL;
-    if (l <= SMALL_MAX_LOG_L || l > POLY_MAX_LOG_L) return POLY_EINVAL;
+    if (l <= SINGLE_SMALL_MAX_LOG_L || l > POLY_MAX_LOG_L) return POLY_EINVAL;
     const Schedule s = schedule_for(l);
     *sigma = s.sigma;
     *C = s.C;

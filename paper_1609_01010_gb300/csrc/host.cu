@@ -338,7 +338,11 @@ Schedule default_schedule(int l) {
         case 20: return Schedule{11, 8};
         case 21:
         case 22: return Schedule{12, 8};
-        default: return l < 14 ? Schedule{10, 8} : Schedule{13, 8};
+        case 10: return Schedule{9, 8};
+        case 11: return Schedule{9, 128};
+        case 12: return Schedule{9, 32};
+        case 13: return Schedule{11, 128};
+        default: return l < 10 ? Schedule{9, 8} : Schedule{13, 8};
     }
 }
 
@@ -347,7 +351,7 @@ bool schedule_valid(int l, Schedule s) {
     if (s.sigma < 9 || s.sigma > 13 || s.sigma > l) return false;
     if (s.C != 8 && s.C != 32 && s.C != 128) return false;
     const int t = l - s.sigma;
-    if (t > 11) return false;
+    if (t < 1 || t > 11) return false;
     if (((int64_t)2 << t) * s.C * 4 > 128 * 1024) return false;
     if (((int64_t)1 << s.sigma) < s.C) return false;
     return true;
@@ -479,7 +483,7 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     PrimeCtx *ctx = nullptr;
     // Small products run with L padded to at least 512 (the product does not
     // depend on L), so their tables must reach depth 9.
-    const bool small = l <= SMALL_MAX_LOG_L;
+    const bool small = l <= SINGLE_SMALL_MAX_LOG_L;
     const int need = (small && l < SMALL_LOG_S) ? SMALL_LOG_S : l;
     int rc = get_prime(p, root, need, &ctx, st);
     if (rc) return rc;

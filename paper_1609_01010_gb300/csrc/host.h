@@ -8,6 +8,13 @@
 
 namespace pm {
 
+// Single products (polymul_mod_async and the entry points built on
+// run_product) with L <= 2^SINGLE_SMALL_MAX_LOG_L run on the one-CTA kernel;
+// longer ones on the three-kernel path, which spreads even a 1024-point
+// product over the whole GPU and measured faster than the one-cluster kernel
+// from L = 1024 up.  Batches keep one CTA per product up to SMALL_MAX_LOG_L.
+constexpr int SINGLE_SMALL_MAX_LOG_L = SMALL_LOG_S;
+
 // Per (device, prime, primitive root): resident twiddle tables and cached
 // ITFT step lists.  Created on first use, never freed before process exit.
 struct PrimeCtx {

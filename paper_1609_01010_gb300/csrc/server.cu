@@ -146,11 +146,10 @@ static uint64_t request_bytes(int64_t za, int64_t zb) {
     const int64_t n = za + zb - 1;
     uint64_t bytes = (uint64_t)(za + zb + n) * 4;
     const int l = ceil_log2(n);
-    if (l > SMALL_MAX_LOG_L)
-        bytes += (uint64_t)std::max(large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true),
-                                    large_workspace_words(n, l, schedule_for(l), true)) *
-                 4;
-    return bytes;
+    int64_t ws = 0;
+    if (l > SMALL_MAX_LOG_L) ws = large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true);
+    if (l > SINGLE_SMALL_MAX_LOG_L) ws = std::max(ws, large_workspace_words(n, l, schedule_for(l), true));
+    return bytes + (uint64_t)ws * 4;
 }
 
 // Launches one admitted group (one prime) on stream si: the requests that

@@ -40,7 +40,7 @@ def crt3(a, b, dev):
     return c.cpu().numpy().view(np.uint32)
 
 
-# one-CTA and cluster paths (L <= 8192), the three-kernel path, ragged tails
+# one-CTA path (L <= 512), the three-kernel path from L = 1024, ragged tails
 SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (64, 64), (300, 1000), (1024, 1024), (3001, 5001),
           (4096, 4097), (10000, 9000), (20000, 13107)]
 
