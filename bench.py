@@ -20,6 +20,8 @@ The same line also carries:
   crt3         exact integer products of 32-bit-coefficient operands (three
                primes and the CRT, Section 1) at z = 2^16, 2^20, 3000001,
                against three modular products of the same size;
+  radix        general-radix products (transform length m 2^k, m = 3, 5, 15)
+               against the power-of-two TFT product between 2^20 and 2^21;
   length_sweep the shape of the paper's Fig. 3: TFT product against the
                power-of-two zero-padded NTT product for n in [2^14, 2^22],
                eight lengths per octave;
@@ -347,7 +349,7 @@ def tft_vs_padded(dev, stream, B):
             out[name + "_us"] = ev_time(f, 500, stream) * 1e3
     out["speedup_vs_padded_16384"] = out["padded_ntt_16384_us"] / out["tft_8192_us"]
     out["speedup_vs_padded_8192"] = out["padded_ntt_8192_us"] / out["tft_8192_us"]
-    out["note"] = ("latency of one product per call (L <= 8192: one cluster launch; 16384: three kernels), "
+    out["note"] = ("latency of one product per call (three kernels each), "
                    "CUDA events over 500 back-to-back calls")
     return out
 
@@ -456,6 +458,43 @@ def crt3(dev, stream, B, mod_us, reps=20):
                "hbm_compulsory_gbs": byt / (ms * 1e-3) / 1e9, "correct_sampled": ok}
         if z in mod_us:
             row["vs_three_mod_products"] = 3 * mod_us[z] / (ms * 1e3)
+        rows.append(row)
+        del A, Bv, C
+        torch.cuda.empty_cache()
+    return rows
+
+
+def radix_sweep(dev, stream, B, reps=20):
+    """General-radix products (transform length m 2^k, odd m) against the
+    power-of-two TFT product (m = 1) mod 2013265921 (p - 1 = 15 2^27) at
+    lengths between 2^20 and 2^21."""
+    import torch
+    p = W.P2
+    rows = []
+    for frac in (1.05, 1.3, 1.6, 1.9):
+        n = int(frac * (1 << 20)) | 1
+        z = (n + 1) // 2
+        a, b = W.operands(W.SEED_BASE + 8, z - 1, z - 1, p)
+        sets = 4
+        A = [dev_u32(a, dev) for _ in range(sets)]
+        Bv = [dev_u32(b, dev) for _ in range(sets)]
+        C = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(sets)]
+        sh = stream.cuda_stream
+        row = {"n": n}
+        ref = None
+        for m in (1, 3, 5, 15):
+            def f(i, m=m):
+                j = i % sets
+                B.polymul_mod_radix_async(p, A[j], z - 1, Bv[j], z - 1, C[j], m, sh)
+            with torch.cuda.stream(stream):
+                for i in range(3):
+                    f(i)
+                ms = ev_time(f, reps, stream)
+            out = C[(reps - 1) % sets].cpu().numpy()
+            if ref is None:
+                ref = out
+            row[f"m{m}_us"] = ms * 1e3
+            row[f"m{m}_identical_to_m1"] = bool(np.array_equal(out, ref))
         rows.append(row)
         del A, Bv, C
         torch.cuda.empty_cache()
@@ -603,7 +642,7 @@ def main():
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load before the timed region")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--skip", default="",
-                    help="comma list of parts to skip: e2e,cpu,padded,sweep,crt3,fig3,batched,serving")
+                    help="comma list of parts to skip: e2e,cpu,padded,sweep,crt3,fig3,radix,batched,serving")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -685,6 +724,8 @@ def main():
             line["crt3"] = crt3(dev, stream, B, mod_us)
         if "fig3" not in skip:
             line["length_sweep"] = length_sweep(dev, stream, B)
+        if "radix" not in skip:
+            line["radix"] = radix_sweep(dev, stream, B)
         if "batched" not in skip:
             line["batched"] = batched(dev, stream, B)
         if "serving" not in skip and args.serve_seconds > 0:

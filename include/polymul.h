@@ -124,7 +124,7 @@ int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const u
  * every single-product call records CUDA events around its kernels on its
  * stream.  polymul_profile_end synchronises those events and returns the
  * summed device time in milliseconds and the number of launches per kernel:
- * index 0 the one-CTA product kernel (L <= 8192), 1 the TFT column stage,
+ * index 0 the one-CTA product kernel (L <= 512), 1 the TFT column stage,
  * 2 the row stage (forward, pointwise, inverse), 3 the ITFT column stage.
  */
 int polymul_profile_begin(void);
@@ -167,6 +167,27 @@ int polymul_negacyclic_async(uint32_t p, const uint32_t *a, int64_t za, const ui
  * pool, released on `stream`; the three products also take their own.
  */
 int polymul_crt3_async(const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c, void *stream);
+
+/*
+ * c = a * b mod p with a transform length L = m 2^k that is not a power of
+ * two: the general-radix TFT that Section 1 cites ([25, 27]) against the
+ * power-of-two stair-case, truncated at the radix-m level as Section 5's
+ * relaxed algorithms truncate.  With N = 2^k the smallest power of two
+ * >= 512 with m N >= n (n = da+db+1) and zeta a primitive m-th root of
+ * unity, x^L - 1 splits into the m factors x^N - zeta^j; the product is
+ * computed from its residues modulo the first ceil(n / N) of them, each a
+ * twisted cyclic convolution of length N (Eq. 11) on the power-of-two
+ * kernels, and recombined by the inverse Vandermonde (for all m factors: the
+ * inverse m-point DFT).  The result equals polymul_mod_async's exactly.
+ *   a, b, c: device buffers of da+1, db+1, da+db+1 words, as polymul_mod.
+ *   m: odd radix in [1, 15] dividing p-1 (for 2013265921 = 15 2^27 + 1:
+ *      3, 5, 15; for 469762049 = 7 2^26 + 1: 7); m = 1 is polymul_mod_async.
+ * POLY_EINVAL for an even m, m > 15 or m not dividing p-1; POLY_ETOO_LONG if
+ * m 2^k does not divide p-1 or N > 2^23.  Workspace: 3 ceil(n/N) N words
+ * from the stream-ordered pool, plus twist tables resident per (p, m, k).
+ */
+int polymul_mod_radix_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                            uint32_t *c, int m, void *stream);
 
 /* ---------------------------------------------------------------- TFT plans */
 typedef struct tft_plan tft_plan;
@@ -263,7 +284,7 @@ int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path);
 int polymul_load_schedules(const char *json_path);
 
 /*
- * The schedule the three-kernel path uses for L = 2^l (l in 14..24): row
+ * The schedule the three-kernel path uses for L = 2^l (l in 10..24): row
  * length 2^(*sigma) and column-tile width *C (autotuned or default).  The
  * paper's counterpart is the DP search's chosen breakdown (Section 4).
  * POLY_EINVAL outside that range, POLY_ENULL for null outputs.

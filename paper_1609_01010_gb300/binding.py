@@ -60,6 +60,7 @@ _SIGS = {
     "polymul_cyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_negacyclic_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_crt3_async": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
+    "polymul_mod_radix_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, ctypes.c_int, vp]),
     "polymul_get_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -286,6 +287,12 @@ def polymul_crt3_async(a, da: int, b, db: int, c, stream=None) -> None:
     """c (3*(da+db+1) words) = a * b over the integers, 32-bit coefficients in,
     96-bit little-endian coefficients out (three primes and the CRT)."""
     _check(lib().polymul_crt3_async(_ptr(a), da, _ptr(b), db, _ptr(c), _stream(stream)), "polymul_crt3_async")
+
+
+def polymul_mod_radix_async(p: int, a, da: int, b, db: int, c, m: int, stream=None) -> None:
+    """c = a * b mod p through a transform length m 2^k (odd radix m)."""
+    _check(lib().polymul_mod_radix_async(p, _ptr(a), da, _ptr(b), db, _ptr(c), m, _stream(stream)),
+           "polymul_mod_radix_async")
 
 
 def polymul_get_schedule(l: int) -> tuple[int, int]:

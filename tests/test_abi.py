@@ -56,6 +56,10 @@ def test_host_side_argument_checks(lib):
     assert L.polymul_crt3_async(None, 3, 16, 3, 16, None) == POLY_ENULL
     assert L.polymul_crt3_async(16, 3, 16, -2, 16, None) == POLY_EINVAL
     assert L.polymul_crt3_async(16, 1 << 23, 16, 1 << 23, 16, None) == -2  # n = 2^24 + 1: POLY_ETOO_LONG
+    # general-radix product: radix checks precede any CUDA call
+    assert L.polymul_mod_radix_async(2013265921, 16, 3, 16, 3, 16, 2, None) == POLY_EINVAL  # even radix
+    assert L.polymul_mod_radix_async(2013265921, 16, 3, 16, 3, 16, 17, None) == POLY_EINVAL  # above 15
+    assert L.polymul_mod_radix_async(2013265921, None, 3, 16, 3, 16, 3, None) == POLY_ENULL
     h = ctypes.c_void_p()
     assert L.tft_plan_create(469762049, 0, 0, 5, ctypes.byref(h)) == POLY_EINVAL
     assert L.tft_plan_create(469762049, 0, 6, 5, ctypes.byref(h)) == POLY_EINVAL
