@@ -46,6 +46,11 @@ __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, M
     pdl_launch_dependents();  // the row kernel may start staging its twiddles
     const u32 words = (u32)C << TL;
     tw.fwd = stage_col_tw<TL>(smem, words, tw.fwd);
+    // Launched with programmatic stream serialization: the operands (and the
+    // workspace, which the stream-ordered pool may hand over from the
+    // previous product) are touched only after the previous kernel on the
+    // stream has completed.
+    pdl_wait();
     const int items = 2 * (int)(d.g.S / C);  // (tile, operand) pairs
     int it = blockIdx.x;
     if (it < items) colf_load<C>(d, it >> 1, it & 1, smem);
@@ -96,6 +101,10 @@ __global__ void __launch_bounds__(COLI_THREADS, 3) k_col_itft(const LargeDesc d,
         __syncthreads();
         coli_compute_ct<A, C, TL>(d, it, smem + kb * words, m, tw, top);
     }
+    // Only now may the next kernel on the stream (the next product's column
+    // kernel) be scheduled: launched at the start, its CTAs would take SM
+    // slots while this kernel still runs and slow mid-size products.
+    pdl_launch_dependents();
 }
 
 // ------------------------------------------------------------ launchers
@@ -127,8 +136,7 @@ static cudaError_t launch_colf_c(const LargeDesc &d, ModParams m, TwTables tw, c
     int grid = 0;
     e = persistent_grid((const void *)k_col_fwd<A, C, TL>, COL_THREADS, smem, 2 * (int)(d.g.S / C), &grid);
     if (e != cudaSuccess) return e;
-    k_col_fwd<A, C, TL><<<grid, COL_THREADS, smem, st>>>(d, m, tw);
-    return cudaGetLastError();
+    return launch_pdl(k_col_fwd<A, C, TL>, grid, COL_THREADS, smem, st, d, m, tw);
 }
 
 template <class A, int C, int TL>
