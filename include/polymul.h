@@ -85,9 +85,13 @@ int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const ui
                              uint32_t *c, int64_t Lp, void *stream);
 
 /*
- * Host-buffer form: a, b, c are host pointers (pinned memory gives the best
- * copy rate).  Copies in, multiplies and copies out on an internal stream;
- * synchronous.
+ * Host-buffer form: a, b, c are host pointers (pinned or pageable).
+ * Synchronous, on an internal stream.  Where the device walks the host's
+ * page tables (address translation services; GB300 with a Grace host, over
+ * NVLink-C2C), products with da+db+1 <= 2^19 are computed on the host
+ * buffers in place and larger ones are staged through device memory by
+ * copy kernels on all SMs; elsewhere the copy engines stage them (pinned
+ * memory gives the best rate).
  */
 int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
 

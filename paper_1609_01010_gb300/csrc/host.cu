@@ -533,6 +533,71 @@ static void keep_pool_memory() {
     });
 }
 
+// Whether kernels on device `dev` may read and write ordinary host memory in
+// place: the device walks the host's page tables (address translation
+// services; on Grace systems over the coherent NVLink-C2C link), so every
+// host address the process can use is also valid in a kernel.  Then the host
+// entry point needs no staging buffers or copies.
+// Host-buffer products with n <= 2^19 words run on the host buffers in place
+// when the device can address them: measured on GB300 (Grace host) end to end
+// 22 / 52 us at n = 2^10 / 2^19 in place against 29 / 57 us with copy kernels
+// and 36 / 65 us with copy engines.  Larger ones are staged: the column
+// kernels' 32-byte row segments use the link poorly (217 against 141 us at
+// n = 2^21), while the copy kernels move it in 16-byte vectors.
+constexpr int64_t HOST_IN_PLACE_MAX_N = (int64_t)1 << 19;
+
+// Copies of up to two segments (src0 -> dst0, n0 words; src1 -> dst1, n1
+// words) by all SMs, 16-byte accesses where both sides allow them; either
+// side may be host memory the device can address.  Four independent
+// accesses per thread keep the link's latency covered.
+__global__ void __launch_bounds__(512) k_copy_words(const u32 *__restrict__ s0, u32 *__restrict__ d0, int64_t n0,
+                                                    const u32 *__restrict__ s1, u32 *__restrict__ d1, int64_t n1) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int seg = 0; seg < 2; ++seg) {
+        const u32 *s = seg ? s1 : s0;
+        u32 *d = seg ? d1 : d0;
+        const int64_t n = seg ? n1 : n0;
+        if (n <= 0) continue;
+        const int64_t head = ((((uintptr_t)s) | ((uintptr_t)d)) & 15) == 0 ? 0 : n;  // words before the vector part
+        const int64_t n4 = (n - head) / 4;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(s + head);
+        uint4 *d4 = reinterpret_cast<uint4 *>(d + head);
+        for (int64_t i = t; i < n4; i += 4 * stride) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * stride < n4) v[u] = s4[i + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * stride < n4) d4[i + u * stride] = v[u];
+        }
+        for (int64_t i = t; i < head; i += stride) d[i] = s[i];
+        for (int64_t i = head + 4 * n4 + t; i < n; i += stride) d[i] = s[i];
+    }
+}
+
+static cudaError_t launch_copy_words(const u32 *s0, u32 *d0, int64_t n0, const u32 *s1, u32 *d1, int64_t n1,
+                                     cudaStream_t st) {
+    const int64_t vec = (std::max(n0, n1) + 3) / 4;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((vec + 511) / 512, 152 * 4));
+    k_copy_words<<<blocks, 512, 0, st>>>(s0, d0, n0, s1, d1, n1);
+    return cudaGetLastError();
+}
+
+static bool host_memory_in_place(int dev) {
+    static std::mutex mu;
+    static std::map<int, bool> known;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find(dev);
+    if (it != known.end()) return it->second;
+    int ats = 0;
+    if (cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
+        cudaGetLastError();
+        ats = 0;
+    }
+    return known[dev] = (ats == 1);
+}
+
 }  // namespace pm
 
 using namespace pm;
@@ -643,15 +708,34 @@ int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *
         st_dev = dev;
     }
     const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    const bool in_place = host_memory_in_place(dev);
+    if (in_place && n <= HOST_IN_PLACE_MAX_N) {
+        // Small products: the kernels read a and b and write c in place.
+        int rc = polymul_mod_async(p, a, da, b, db, c, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
+        return rc;
+    }
+    // staging buffers at 16-byte boundaries (vector copies)
+    const int64_t za4 = (za + 3) & ~(int64_t)3, zb4 = (zb + 3) & ~(int64_t)3;
     u32 *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, (size_t)(za + zb + n) * 4, st) != cudaSuccess) return POLY_ENOMEM;
-    u32 *da_ = buf, *db_ = buf + za, *dc_ = buf + za + zb;
+    if (cudaMallocAsync((void **)&buf, (size_t)(za4 + zb4 + n) * 4, st) != cudaSuccess) return POLY_ENOMEM;
+    u32 *da_ = buf, *db_ = buf + za4, *dc_ = buf + za4 + zb4;
     int rc = POLY_OK;
-    if (cudaMemcpyAsync(da_, a, (size_t)za * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(db_, b, (size_t)zb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (in_place) {
+        // Every SM moves 16-byte vectors over the coherent link.
+        if (launch_copy_words(a, da_, za, b, db_, zb, st) != cudaSuccess) rc = POLY_ECUDA;
+    } else if (cudaMemcpyAsync(da_, a, (size_t)za * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+               cudaMemcpyAsync(db_, b, (size_t)zb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         rc = POLY_ECUDA;
+    }
     if (!rc) rc = polymul_mod_async(p, da_, da, db_, db, dc_, st);
-    if (!rc && cudaMemcpyAsync(c, dc_, (size_t)n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = POLY_ECUDA;
+    if (!rc) {
+        if (in_place) {
+            if (launch_copy_words(dc_, c, n, nullptr, nullptr, 0, st) != cudaSuccess) rc = POLY_ECUDA;
+        } else if (cudaMemcpyAsync(c, dc_, (size_t)n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            rc = POLY_ECUDA;
+        }
+    }
     cudaFreeAsync(buf, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
     return rc;

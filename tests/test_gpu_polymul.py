@@ -232,8 +232,30 @@ def test_errors_are_returned(gpu):
 
 
 def test_host_buffer_entry_point(gpu, orc):
+    """polymul_mod_host on pageable numpy buffers, on pinned buffers, on
+    buffers at odd word offsets (no 16-byte alignment), one-CTA and
+    three-kernel sizes, twice in a row on the same buffers."""
+    import torch
     from paper_1609_01010_gb300 import binding as B
-    p, a, b = W.workload2()
-    c = np.zeros(len(a) + len(b) - 1, dtype=np.uint32)
-    B.polymul_mod_host(p, a, len(a) - 1, b, len(b) - 1, c)
-    assert np.array_equal(c, orc.polymul_tft(p, a, b))
+    # n up to 2^19 - 1 runs in place where the device walks the host page
+    # tables; n = 2^20 - 1 is staged by copy kernels (copy engines elsewhere)
+    cases = [W.workload2(), W.workload1(), (W.P1,) + W.operands(W.SEED_BASE + 90, 100, 37, W.P1),
+             W.workload3(1 << 18), W.workload3(1 << 19)]
+    for p, a, b in cases:
+        n = len(a) + len(b) - 1
+        want = orc.polymul_tft(p, a, b)
+        c = np.zeros(n, dtype=np.uint32)
+        B.polymul_mod_host(p, a, len(a) - 1, b, len(b) - 1, c)
+        assert np.array_equal(c, want)
+        ha = torch.from_numpy(a.view(np.int32)).pin_memory()
+        hb = torch.from_numpy(b.view(np.int32)).pin_memory()
+        hc = torch.zeros(n + 1, dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            B.polymul_mod_host(p, ha.data_ptr(), len(a) - 1, hb.data_ptr(), len(b) - 1, hc.data_ptr() + 4)
+            assert np.array_equal(hc.numpy()[1:].view(np.uint32), want)
+        # odd offsets: a and b one word into larger buffers
+        a2 = np.concatenate([[7], a]).astype(np.uint32)
+        b2 = np.concatenate([[9], b]).astype(np.uint32)
+        c2 = np.zeros(n + 3, dtype=np.uint32)
+        B.polymul_mod_host(p, a2.ctypes.data + 4, len(a) - 1, b2.ctypes.data + 4, len(b) - 1, c2.ctypes.data + 12)
+        assert np.array_equal(c2[3:], want) and not c2[:3].any()
