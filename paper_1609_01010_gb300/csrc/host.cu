@@ -478,12 +478,12 @@ int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune) {
 }
 
 int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                cudaStream_t st, u32 *workspace, int64_t n_out) {
+                cudaStream_t st, u32 *workspace, int64_t n_out, int small_max_l) {
     if (!a || !b || !c) return POLY_ENULL;
     PrimeCtx *ctx = nullptr;
     // Small products run with L padded to at least 512 (the product does not
     // depend on L), so their tables must reach depth 9.
-    const bool small = l <= SINGLE_SMALL_MAX_LOG_L;
+    const bool small = l <= std::min(small_max_l, SMALL_MAX_LOG_L);
     const int need = (small && l < SMALL_LOG_S) ? SMALL_LOG_S : l;
     int rc = get_prime(p, root, need, &ctx, st);
     if (rc) return rc;

@@ -12,7 +12,10 @@ namespace pm {
 // run_product) with L <= 2^SINGLE_SMALL_MAX_LOG_L run on the one-CTA kernel;
 // longer ones on the three-kernel path, which spreads even a 1024-point
 // product over the whole GPU and measured faster than the one-cluster kernel
-// from L = 1024 up.  Batches keep one CTA per product up to SMALL_MAX_LOG_L.
+// from L = 1024 up (8.2 against 10.4 us at L = 8192).  Where many products
+// overlap on the GPU, one launch on a few SMs per small product leaves the
+// rest of the GPU to the others: batches keep one CTA per product and the
+// server one cluster per product up to SMALL_MAX_LOG_L.
 constexpr int SINGLE_SMALL_MAX_LOG_L = SMALL_LOG_S;
 
 // Per (device, prime, primitive root): resident twiddle tables and cached
@@ -70,7 +73,10 @@ int prepare_small(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t
 int prepare_large(PrimeCtx *ctx, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
                   Schedule sch, LargeDesc *d, int64_t n_out = -1);
 int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune);
+// small_max_l: the largest log2 L that runs on the one-CTA / one-cluster
+// kernel (the public single-product entry points use SINGLE_SMALL_MAX_LOG_L;
+// the server, whose requests overlap on the GPU, SMALL_MAX_LOG_L).
 int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
-                cudaStream_t st, u32 *workspace, int64_t n_out = -1);
+                cudaStream_t st, u32 *workspace, int64_t n_out = -1, int small_max_l = SINGLE_SMALL_MAX_LOG_L);
 
 }  // namespace pm

@@ -146,10 +146,11 @@ static uint64_t request_bytes(int64_t za, int64_t zb) {
     const int64_t n = za + zb - 1;
     uint64_t bytes = (uint64_t)(za + zb + n) * 4;
     const int l = ceil_log2(n);
-    int64_t ws = 0;
-    if (l > SMALL_MAX_LOG_L) ws = large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true);
-    if (l > SINGLE_SMALL_MAX_LOG_L) ws = std::max(ws, large_workspace_words(n, l, schedule_for(l), true));
-    return bytes + (uint64_t)ws * 4;
+    if (l > SMALL_MAX_LOG_L)
+        bytes += (uint64_t)std::max(large_workspace_words(n, l, Schedule{BATCH_SIGMA, 16}, true),
+                                    large_workspace_words(n, l, schedule_for(l), true)) *
+                 4;
+    return bytes;
 }
 
 // Launches one admitted group (one prime) on stream si: the requests that
@@ -240,7 +241,8 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
         }
     }
     for (auto &r : plain) {
-        const int rc = run_product(r.p, 0, r.a, r.za, r.b, r.zb, r.c, ceil_log2(r.n), true, ss.st, nullptr);
+        const int rc = run_product(r.p, 0, r.a, r.za, r.b, r.zb, r.c, ceil_log2(r.n), true, ss.st, nullptr, -1,
+                                   SMALL_MAX_LOG_L);
         if (rc) {
             if (L->dbuf) cudaFreeAsync(L->dbuf, ss.st);
             delete L;
