@@ -700,6 +700,17 @@ def main():
                 "kernel_us_per_step": {"col_tft": prof_ms[1] / max(1, prof_cnt[1]) * 1e3,
                                        "rows": row_ms * 1e3,
                                        "col_itft": prof_ms[3] / max(1, prof_cnt[3]) * 1e3}}
+    # The whole product against the same peak: the column stages' butterflies
+    # (TFT: t - 1 levels of both operands, the top one a copy since the upper
+    # half of each operand is zero; ITFT: t levels of the product) plus the
+    # row stage's operations, over the step time.
+    t_col = 21 - sch_sigma
+    col_bfly = 2 * (1 << 20) * (t_col - 1) + (1 << 20) * t_col
+    prod_ops = col_bfly * ops_per_bfly + ops_per_launch
+    roofline["product"] = {"algorithmic_ops": prod_ops, "achieved": prod_ops / (ms * 1e-3) / 1e12,
+                           "frac": prod_ops / (ms * 1e-3) / 1e12 / peak_tops,
+                           "note": "all three kernels' butterflies (7 ops) and pointwise products (11 ops) "
+                                   "per step time, against the same integer-issue peak"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     comp_bytes = 4 * (2 * z + n)
     line = {"metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
