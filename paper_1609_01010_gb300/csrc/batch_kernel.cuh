@@ -27,7 +27,8 @@ template <class A, int C>
 // Three resident CTAs per SM (at most 85 registers a thread; the largest
 // item's shared memory, 64 KB for a 16-row one-CTA product, allows three):
 // the items' barrier and load waits are latency-bound, and the extra CTA per
-// SM made the 4096-product batch 21 % faster than two CTAs with no spills.
+// SM made the 4096-product batch 21 % faster than two CTAs, although the
+// one-CTA product bodies then spill a few hundred bytes to local memory.
 __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
     __shared__ int s_item, s_ok;
     for (;;) {
