@@ -20,7 +20,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "host.h"
 #include "polymul.h"
@@ -131,40 +130,9 @@ static int elementwise_grid(int64_t items) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
 }
 
-// Two auxiliary streams and three events per host thread and device: the
-// products mod q1 and q2 run on the auxiliary streams, forked from and
-// joined back into the caller's stream by events, so the three products
-// overlap on the GPU (their kernels fill each other's idle SM time).
-struct CrtStreams {
-    int dev = -1;
-    cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
-};
-
-static int crt_streams(CrtStreams **out) {
-    static thread_local std::vector<CrtStreams> per_dev;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    for (auto &x : per_dev)
-        if (x.dev == dev) {
-            *out = &x;
-            return POLY_OK;
-        }
-    CrtStreams x;
-    x.dev = dev;
-    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamCreateWithFlags(&x.aux[j], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
-    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&x.join[j], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "three-primes streams");
-    per_dev.push_back(x);
-    *out = &per_dev.back();
-    return POLY_OK;
-}
-
 static int crt3(const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, cudaStream_t st) {
-    CrtStreams *cs = nullptr;
-    int rs = crt_streams(&cs);
+    AuxStreams *cs = nullptr;  // the products mod q1 and q2 run on cs->s[0], cs->s[1]
+    int rs = aux_streams(&cs);
     if (rs) return rs;
     const int64_t n = za + zb - 1;
     const int l = ceil_log2(n);
@@ -185,7 +153,7 @@ static int crt3(const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, cuda
     const u32 primes[3] = {crt::Q0, crt::Q1, crt::Q2};
     if (rc == POLY_OK && (e = cudaEventRecord(cs->fork, st)) != cudaSuccess) rc = cuda_fail(e, "fork event");
     for (int j = 0; j < 3 && rc == POLY_OK; ++j) {
-        cudaStream_t sj = j == 0 ? st : cs->aux[j - 1];
+        cudaStream_t sj = j == 0 ? st : cs->s[j - 1];
         if (j > 0 && (e = cudaStreamWaitEvent(sj, cs->fork, 0)) != cudaSuccess) {
             rc = cuda_fail(e, "fork wait");
             break;

@@ -25,6 +25,29 @@ int cuda_fail(cudaError_t e, const char *where) {
 }
 
 // ------------------------------------------------------------ host math
+int aux_streams(AuxStreams **out) {
+    static thread_local std::vector<AuxStreams> per_dev;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    for (auto &x : per_dev)
+        if (x.dev == dev) {
+            *out = &x;
+            return POLY_OK;
+        }
+    AuxStreams x;
+    x.dev = dev;
+    for (int j = 0; j < AUX_STREAMS && e == cudaSuccess; ++j)
+        e = cudaStreamCreateWithFlags(&x.s[j], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
+    for (int j = 0; j < AUX_STREAMS && e == cudaSuccess; ++j)
+        e = cudaEventCreateWithFlags(&x.join[j], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "auxiliary streams");
+    per_dev.push_back(x);
+    *out = &per_dev.back();
+    return POLY_OK;
+}
+
 u32 h_powmod(u64 b, u64 e, u32 p) {
     u64 r = 1 % p;
     b %= p;

@@ -41,6 +41,19 @@ struct PrimeCtx {
 // and returns POLY_ECUDA.
 int cuda_fail(cudaError_t e, const char *where);
 
+// Auxiliary streams of the calling host thread on the current device, for
+// entry points that fork independent products off the caller's stream and
+// join them back (the three primes algorithm, the general radix): non-
+// blocking streams, a fork event and one join event per stream.  Created on
+// first use, kept until the process exits.
+constexpr int AUX_STREAMS = 3;
+struct AuxStreams {
+    int dev = -1;
+    cudaStream_t s[AUX_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[AUX_STREAMS] = {};
+};
+int aux_streams(AuxStreams **out);
+
 u32 h_powmod(u64 b, u64 e, u32 p);
 u32 h_invmod(u32 a, u32 p);
 uint2 shoup_pair(u32 w, u32 p);

@@ -243,34 +243,6 @@ static bool vandermonde_inverse(u32 z, int r, u32 p, u32 out[radix::MAXM][radix:
     return true;
 }
 
-// Auxiliary streams for the m2 convolutions (per host thread and device).
-struct RadixStreams {
-    int dev = -1;
-    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
-};
-
-static int radix_streams(RadixStreams **out) {
-    static thread_local std::vector<RadixStreams> per_dev;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    for (auto &x : per_dev)
-        if (x.dev == dev) {
-            *out = &x;
-            return POLY_OK;
-        }
-    RadixStreams x;
-    x.dev = dev;
-    for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = cudaStreamCreateWithFlags(&x.aux[j], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
-    for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&x.join[j], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "radix streams");
-    per_dev.push_back(x);
-    *out = &per_dev.back();
-    return POLY_OK;
-}
-
 static int radix_product(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int m, cudaStream_t st) {
     u32 root = 0;
     int rc = validate_prime(p, &root);
@@ -286,8 +258,8 @@ static int radix_product(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t 
     RadixTables *T = nullptr;
     rc = radix_tables(p, root, m, k, st, &T);
     if (rc) return rc;
-    RadixStreams *rs = nullptr;
-    rc = radix_streams(&rs);
+    AuxStreams *rs = nullptr;
+    rc = aux_streams(&rs);
     if (rc) return rc;
 
     RadixParams P{};
@@ -320,10 +292,10 @@ static int radix_product(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t 
     e = launch_radix(true, a, b, res, P, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "radix fold launch");
     if (rc == POLY_OK && (e = cudaEventRecord(rs->fork, st)) != cudaSuccess) rc = cuda_fail(e, "fork event");
-    bool used[3] = {false, false, false};
+    bool used[AUX_STREAMS] = {};
     for (int j = 0; j < m2 && rc == POLY_OK; ++j) {
-        const int s = j % 4;  // stream 0 = the caller's, 1..3 auxiliary
-        cudaStream_t sj = s == 0 ? st : rs->aux[s - 1];
+        const int s = j % (AUX_STREAMS + 1);  // stream 0 = the caller's, then the auxiliary ones
+        cudaStream_t sj = s == 0 ? st : rs->s[s - 1];
         if (s > 0 && !used[s - 1]) {
             if ((e = cudaStreamWaitEvent(sj, rs->fork, 0)) != cudaSuccess) {
                 rc = cuda_fail(e, "fork wait");
@@ -334,9 +306,9 @@ static int radix_product(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t 
         rc = run_product(p, 0, res + (size_t)j * N, N, res + (size_t)(m2 + j) * N, N, prod + (size_t)j * N, k, true,
                          sj, nullptr, N);
     }
-    for (int s = 0; s < 3 && rc == POLY_OK; ++s) {
+    for (int s = 0; s < AUX_STREAMS && rc == POLY_OK; ++s) {
         if (!used[s]) continue;
-        if ((e = cudaEventRecord(rs->join[s], rs->aux[s])) != cudaSuccess ||
+        if ((e = cudaEventRecord(rs->join[s], rs->s[s])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(st, rs->join[s], 0)) != cudaSuccess)
             rc = cuda_fail(e, "join event");
     }
