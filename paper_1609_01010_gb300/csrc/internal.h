@@ -68,7 +68,7 @@ constexpr int SMALL_LOG_S = 9;
 constexpr int SMALL_MAX_LOG_T = 4;
 constexpr int SMALL_MAX_LOG_L = SMALL_LOG_S + SMALL_MAX_LOG_T;
 
-// Large products: rows of S = 2^sigma (11..13) words handled by one CTA each,
+// Large products: rows of S = 2^sigma (9..13) words handled by one CTA each,
 // column tiles of C words handled by one CTA each, T <= 1024 rows.
 constexpr int LARGE_MAX_LOG_T = 10;
 // Rows computed by the three-kernel path: ceil(n/S) rounded up to a multiple
@@ -106,7 +106,8 @@ cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int item
 // Kernels are launched only through these (defined in k_small.cu /
 // k_large.cu / k_generic.cu); all return a cudaError_t of the launch.
 
-// One CTA per product; used for l <= SMALL_MAX_LOG_L (l < 9 is padded to 9).
+// One CTA (or, for one product of T >= 2 rows, one cluster) per product; used
+// for the products that take the small path (l < 9 is padded to 9).
 struct SmallDesc {
     const uint32_t *a, *b;
     uint32_t *c;

@@ -1,4 +1,5 @@
-// k_large.cu -- the three-kernel path for transform lengths L >= 16384.
+// k_large.cuh -- the three-kernel path (single products from L = 1024 up;
+// in batches and the server from L = 16384 up).
 //
 // L = T * S with rows of S = 2^sigma words (sigma = 9..13) and T <= 2048.
 //   k_col_fwd   grid (S/C, 2): column stage of TFT(a) and TFT(b) on tiles of
@@ -11,6 +12,8 @@
 //               else the truncated one of coli_tile_ct), then the first n
 //               outputs reduced to [0, p).
 // Each kernel reads its inputs once from HBM/L2 and writes its outputs once.
+// All three are launched with programmatic stream serialization: each stages
+// its twiddles before waiting for the previous kernel (griddepcontrol.wait).
 #pragma once
 #include "bodies.cuh"
 

@@ -1,5 +1,6 @@
-// k_small.cu -- one CTA per product for transform lengths L <= 8192 (a
-// single product of L >= 1024 runs on a cluster instead: k_small_cl.cuh).
+// k_small.cuh -- one CTA per product for transform lengths L <= 8192 (a
+// launch for one product of L >= 1024 -- a server request or the
+// allocation-free entry point -- runs on a cluster instead: k_small_cl.cuh).
 //
 // The product is laid out as T = L/512 rows of 512 words in shared memory
 // (operands a and b side by side).  Steps, all in one launch:
