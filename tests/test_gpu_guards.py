@@ -94,7 +94,7 @@ def test_product_entry_points_stay_inside_their_buffers(gpu, orc, za, zb):
         assert np.array_equal(c, want), name
 
 
-@pytest.mark.parametrize("N", [5, 512, 1000, 4096, 65536])
+@pytest.mark.parametrize("N", [5, 512, 1000, 4096, 16384])
 def test_convolutions_stay_inside_their_buffers(gpu, orc, N):
     from paper_1609_01010_gb300 import binding as B
     p = W.P2
