@@ -267,3 +267,46 @@ def test_golden_tiny_products(orc):
     for r in recs:
         assert orc.polymul_tft(r["p"], r["a"], r["b"]).tolist() == r["c"]
         assert orc.schoolbook(r["p"], r["a"], r["b"]).tolist() == r["c"]
+
+
+@pytest.mark.parametrize("p,g", PRIMES)
+def test_batch_equals_kronecker_per_product(orc, p, g):
+    """The batched oracle (the checker of the GPU batch) product by product
+    against Kronecker substitution: ragged lengths (1 to a few hundred), a
+    non-zero first offset in a, b and c, and gaps in c between products whose
+    words must stay untouched."""
+    import ctypes
+    rng = random.Random(31 + p % 97)
+    sizes = [(1, 1), (7, 300), (129, 2), (64, 64), (513, 17), (1, 250), (200, 1), (33, 95)]
+    a_off, b_off, c_off = [5], [11], [3]
+    for i, (za, zb) in enumerate(sizes):
+        a_off.append(a_off[-1] + za)
+        b_off.append(b_off[-1] + zb)
+        c_off.append(c_off[-1] + za + zb - 1 + (i % 3))  # 0, 1 or 2 unused words after product i
+    a = rnd(rng, a_off[-1], p)
+    b = rnd(rng, b_off[-1], p)
+    sentinel = 0xA5A5A5A5
+    c = np.full(c_off[-1] + 4, sentinel, dtype=np.uint32)
+    i64 = lambda x: np.ascontiguousarray(x, dtype=np.int64)
+    ao, bo, co = i64(a_off), i64(b_off), i64(c_off)
+    P = ctypes.POINTER(ctypes.c_uint32)
+    Q = ctypes.POINTER(ctypes.c_int64)
+    rc = orc.lib().or_polymul_tft_batch(p, g, len(sizes), a.ctypes.data_as(P), ao.ctypes.data_as(Q),
+                                        b.ctypes.data_as(P), bo.ctypes.data_as(Q), c.ctypes.data_as(P),
+                                        co.ctypes.data_as(Q))
+    assert rc == 0
+    written = np.zeros(len(c), dtype=bool)
+    for i, (za, zb) in enumerate(sizes):
+        ai = a[a_off[i]:a_off[i] + za]
+        bi = b[b_off[i]:b_off[i] + zb]
+        n = za + zb - 1
+        assert c[c_off[i]:c_off[i] + n].tolist() == brute.kronecker_product(ai, bi, p), i
+        written[c_off[i]:c_off[i] + n] = True
+    assert (c[~written] == sentinel).all()  # the first 3 words, the gaps and the tail
+    # the wrapper: same products through numpy offsets
+    got = orc.polymul_tft_batch(p, a, a_off, b, b_off, c_off)
+    assert np.array_equal(got[written[:len(got)]], c[:len(got)][written[:len(got)]])
+    # a plausible offset mistake (operand b of product i taken from product
+    # i+1's start) is caught by the per-product comparison above
+    wrong = orc.polymul_tft(p, a[a_off[1]:a_off[2]], b[b_off[2]:b_off[2] + sizes[1][1]])
+    assert wrong.tolist() != brute.kronecker_product(a[a_off[1]:a_off[2]], b[b_off[1]:b_off[2]], p)
