@@ -35,6 +35,7 @@ _SIGS = {
     "polymul_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "polymul_version": (ctypes.c_char_p, []),
     "polymul_last_error": (ctypes.c_char_p, []),
+    "polymul_device_status": (ctypes.c_int, [ctypes.c_int]),
     "polymul_mod": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
     "polymul_mod_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_mod_padded_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
@@ -42,6 +43,8 @@ _SIGS = {
     "polymul_mod_noalloc_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_profile_begin": (ctypes.c_int, []),
     "polymul_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), I64P]),
+    "polymul_probe_int": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "tft_plan_create": (ctypes.c_int, [u32, u32, i64, i64, ctypes.POINTER(vp)]),
     "tft_plan_length": (i64, [vp]),
     "tft_exec": (ctypes.c_int, [vp, vp, vp, vp]),
@@ -86,6 +89,11 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def polymul_device_status(clear: bool = False) -> int:
+    """The current device's status word (0, POLY_ETIMEOUT or POLY_EINVAL_COEF)."""
+    return int(lib().polymul_device_status(1 if clear else 0))
 
 
 def strerror(status: int) -> str:
@@ -163,6 +171,18 @@ def polymul_profile_end() -> tuple[list[float], list[int]]:
     n = (ctypes.c_int64 * 4)()
     _check(lib().polymul_profile_end(ms, n), "polymul_profile_end")
     return list(ms), list(n)
+
+
+PROBE_KINDS = {0: "forward butterfly", 1: "inverse butterfly", 2: "mul.lo.u32", 3: "mul.hi.u32", 4: "add.u32",
+               5: "min.u32"}
+
+
+def polymul_probe_int(kind: int, iters: int = 1 << 14) -> tuple[float, float]:
+    """(operations per second, ms of the timed launch) of integer probe `kind`."""
+    ops = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().polymul_probe_int(kind, iters, ctypes.byref(ops), ctypes.byref(ms)), "polymul_probe_int")
+    return ops.value, ms.value
 
 
 # ------------------------------------------------------------ TFT plans

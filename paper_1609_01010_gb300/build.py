@@ -50,10 +50,15 @@ def _variants() -> dict[str, list[tuple[str, list[str]]]]:
     cols = []
     for fwd in (1, 0):
         for lazy in (1, 0):
-            for c in (8, 32, 128):
+            for c in (8, 128):  # 32-column tiles run the TMA-fed kernels of k_cols_tma.cu
                 name = f"launch_col{'f' if fwd else 'i'}_{'lazy' if lazy else 'strict'}_c{c}"
                 cols.append((name, [f"-DPM_FWD={fwd}", f"-DPM_LAZY={lazy}", f"-DPM_C={c}", f"-DPM_COL_FN={name}"]))
-    return {"k_cols.cu": cols}
+    tcols = []
+    for fwd in (1, 0):
+        for lazy in (1, 0):
+            name = f"launch_tcol{'f' if fwd else 'i'}_{'lazy' if lazy else 'strict'}"
+            tcols.append((name, [f"-DPM_FWD={fwd}", f"-DPM_LAZY={lazy}", f"-DPM_TCOL_FN={name}"]))
+    return {"k_cols.cu": cols, "k_cols_tma.cu": tcols}
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

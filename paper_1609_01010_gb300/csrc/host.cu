@@ -110,6 +110,29 @@ static u32 default_root(u32 p) {
     return 0;
 }
 
+// ------------------------------------------------------------ device status
+// One word per device that kernels set when a bounded wait expires (or, in
+// validating runs, when an input is out of range).  A static device variable,
+// so fetching it never allocates.
+static __device__ int g_pm_status;
+
+int *device_status_ptr() {
+    static std::mutex mu;
+    static std::map<int, int *> ptrs;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = ptrs.find(dev);
+    if (it != ptrs.end()) return it->second;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pm_status) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    ptrs[dev] = (int *)p;
+    return (int *)p;
+}
+
 // ------------------------------------------------------------ prime registry
 static std::mutex g_mu;
 static std::map<std::tuple<int, u32, u32>, PrimeCtx *> g_primes;
@@ -210,6 +233,7 @@ int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st) {
             return POLY_ECUDA;
         }
         ctx->tw.pscale = ctx->pscale;
+        ctx->tw.status = device_status_ptr();
         g_primes[key] = ctx;
     } else {
         ctx = it->second;
@@ -369,13 +393,14 @@ Schedule default_schedule(int l) {
     }
 }
 
-// Column tiles are double-buffered: 2 * T * C words must fit 128 KB.
+// Column tiles are double-buffered: 2 * T * C words must fit 128 KB.  The
+// TMA-fed kernels of 32-column tiles also take t = 10 (one 128 KB stage).
 bool schedule_valid(int l, Schedule s) {
     if (s.sigma < 9 || s.sigma > 13 || s.sigma > l) return false;
     if (s.C != 8 && s.C != 32 && s.C != 128) return false;
     const int t = l - s.sigma;
     if (t < 1 || t > 11) return false;
-    if (((int64_t)2 << t) * s.C * 4 > 128 * 1024) return false;
+    if (((int64_t)2 << t) * s.C * 4 > 128 * 1024 && !(s.C == 32 && t == 10)) return false;
     if (((int64_t)1 << s.sigma) < s.C) return false;
     return true;
 }
@@ -640,6 +665,7 @@ const char *polymul_strerror(int s) {
         case POLY_EINVAL: return "argument out of range";
         case POLY_EBUSY: return "request exceeds the server memory budget";
         case POLY_ENOTFOUND: return "unknown ticket";
+        case POLY_EINVAL_COEF: return "an input coefficient is outside [0, p)";
         default: return "unknown status";
     }
 }
@@ -647,6 +673,18 @@ const char *polymul_strerror(int s) {
 const char *polymul_version(void) { return "gb300-polymul 0.1 (sm_103a)"; }
 
 const char *polymul_last_error(void) { return g_last_err; }
+
+int polymul_device_status(int clear) {
+    int *p = device_status_ptr();
+    if (!p) return POLY_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return POLY_ECUDA;
+    if (clear && v != 0) {
+        const int zero = 0;
+        if (cudaMemcpy(p, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return POLY_ECUDA;
+    }
+    return v;
+}
 
 int polymul_profile_begin(void) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -22,7 +22,12 @@ struct TwTables {
     const uint2 *inv;
     int lmax;             // entries [1, 2^lmax) are valid
     const uint2 *pscale;  // pscale[e] = Shoup pair of 2^32 * 2^-e mod p, e < 32
+    int *status = nullptr;  // the device status word (bounded waits record POLY_ETIMEOUT)
 };
+
+// The device status word of the current device (a static device variable of
+// the library; its address is fetched once per device).  NULL on failure.
+int *device_status_ptr();
 
 __host__ __device__ inline uint32_t tw_index(int level, uint32_t node) { return (1u << level) + node; }
 

@@ -2,7 +2,8 @@
 //
 // Compiled once per variant by build.py with
 //   PM_LAZY (1: p < 2^30 regime, 0: word-bound), PM_FWD (1: TFT column
-//   stage, 0: ITFT column stage), PM_C (tile width 8, 32 or 128) and
+//   stage, 0: ITFT column stage), PM_C (tile width 8 or 128; 32-column tiles run the kernels of
+//   k_cols_tma.cu) and
 //   PM_COL_FN (the name of the launcher this variant defines),
 // so the instantiations (one kernel per column depth t = 1..11) compile in
 // parallel.

@@ -18,6 +18,7 @@
 
 #include <map>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "host.h"
@@ -134,23 +135,38 @@ static int na_setup(int dev, NaDevice &D) {
     if (all.size() > NA_MAX_STEPS) return POLY_ENOMEM;
     e = cudaMemcpy(D.steps, all.data(), all.size() * sizeof(ItftStep), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "step lists");
+    // A copy from pageable host memory may return once the data is staged,
+    // before it has landed in g_na_steps; the caller's stream may be a
+    // non-blocking one that does not wait for the legacy stream.  Wait here.
+    e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "step lists");
     (void)dev;
     D.ready = true;
     return POLY_OK;
+}
+
+// The step list recorded for (T, k) of prime pi, or false if set-up did not
+// record one (a geometry outside the ranges na_setup enumerates).
+static bool na_list(const NaDevice &D, int pi, int64_t T, int64_t k, std::pair<int, int> *out) {
+    auto it = D.lists[pi].find(std::make_pair(T, k));
+    if (it == D.lists[pi].end()) return false;
+    *out = it->second;
+    return true;
 }
 
 }  // namespace pm
 
 using namespace pm;
 
-extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
-                                         uint32_t *c, void *stream) {
+static int noalloc_body(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                        void *stream) {
     if (!a || !b || !c) return POLY_ENULL;
     if (da < 0 || db < 0) return POLY_EINVAL;
     const int pi = p == NA_PRIMES[0] ? 0 : (p == NA_PRIMES[1] ? 1 : -1);
     if (pi < 0) return POLY_EINVAL_PRIME;
+    // da + db + 1 <= 2^17 checked before any addition (no signed overflow)
+    if (da >= ((int64_t)1 << NA_MAX_LOG_L) || db >= ((int64_t)1 << NA_MAX_LOG_L) - da) return POLY_ETOO_LONG;
     const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
-    if (n > ((int64_t)1 << NA_MAX_LOG_L)) return POLY_ETOO_LONG;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -170,6 +186,7 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
     tw.inv = tw.fwd + NA_TW_ENTRIES;
     tw.lmax = NA_MAX_LOG_L;
     tw.pscale = D->pscale + pi * 32;
+    tw.status = device_status_ptr();
     const int l = ceil_log2(n);
     cudaStream_t st = (cudaStream_t)stream;
     if (l <= SMALL_MAX_LOG_L) {
@@ -177,7 +194,8 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
         const int logT = lp - SMALL_LOG_S;
         const int64_t T = (int64_t)1 << logT, S = (int64_t)1 << SMALL_LOG_S;
         const int64_t k = (n + S - 1) / S;
-        const auto &ls = D->lists[pi].at(std::make_pair(T, k));
+        std::pair<int, int> ls;
+        if (!na_list(*D, pi, T, k, &ls)) return POLY_EINVAL;
         SmallDesc d;
         d.a = a;
         d.b = b;
@@ -194,7 +212,8 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
         return e == cudaSuccess ? POLY_OK : cuda_fail(e, "one-CTA product launch");
     }
     const Geometry g = make_geometry(n, l, NA_SIGMA);
-    const auto &ls = D->lists[pi].at(std::make_pair(g.T, g.k));
+    std::pair<int, int> ls;
+    if (!na_list(*D, pi, g.T, g.k, &ls)) return POLY_EINVAL;
     LargeDesc d;
     d.a = a;
     d.b = b;
@@ -210,4 +229,17 @@ extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t 
     d.prune = 1;
     e = launch_large(lazy, d, Schedule{NA_SIGMA, NA_C}, m, tw, st);
     return e == cudaSuccess ? POLY_OK : cuda_fail(e, "three-kernel product launch");
+}
+
+extern "C" int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db,
+                                         uint32_t *c, void *stream) {
+    // No C++ exception may leave an extern "C" function: the host-side maps
+    // of the first call's set-up can throw std::bad_alloc.
+    try {
+        return noalloc_body(p, a, da, b, db, c, stream);
+    } catch (const std::bad_alloc &) {
+        return POLY_ENOMEM;
+    } catch (...) {
+        return POLY_EINVAL;
+    }
 }

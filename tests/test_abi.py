@@ -67,5 +67,9 @@ def test_host_side_argument_checks(lib):
     assert L.polymul_server_create(1 << 20, 4, 2, ctypes.byref(srv)) == POLY_EINVAL  # unknown mode
     assert L.polymul_server_create(1 << 20, 0, 0, ctypes.byref(srv)) == POLY_EINVAL  # no stream
     assert L.polymul_server_create(0, 4, 0, ctypes.byref(srv)) == POLY_EINVAL  # no budget
+    d1, d2 = ctypes.c_double(), ctypes.c_double()
+    assert L.polymul_probe_int(6, 1000, ctypes.byref(d1), ctypes.byref(d2)) == POLY_EINVAL  # unknown kind
+    assert L.polymul_probe_int(0, 0, ctypes.byref(d1), ctypes.byref(d2)) == POLY_EINVAL  # no iterations
+    assert L.polymul_probe_int(0, 1000, None, ctypes.byref(d2)) == POLY_ENULL
     assert L.polymul_strerror(-6).decode().startswith("a bounded wait")
     assert b"sm_103a" in L.polymul_version()

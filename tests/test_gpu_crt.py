@@ -97,6 +97,29 @@ def test_crt3_largest_length_closed_form(gpu):
     assert np.array_equal(c, want)
 
 
+def test_crt3_random_near_2_24(gpu, orc):
+    """Random 32-bit operands with za + zb - 1 = 2^24 - 1000 (L = 2^24, the
+    largest length): every coefficient mod 167772161 (a prime outside the
+    three the algorithm uses, so its residues check the recombination itself)
+    against the modular oracle, and 40 coefficients exactly (Eq. (2) over Z)."""
+    from oracle import brute
+    q = 167772161  # 5 * 2^25 + 1
+    assert brute.is_primitive_root(3, q)
+    za, zb = 1 << 23, (1 << 23) - 999
+    a, b = W.workload6(za, zb)
+    c = crt3(a, b, gpu)
+    n = za + zb - 1
+    assert c.shape == (n, 3)
+    ks = [0, 1, zb - 1, za - 1, n - 2, n - 1] + [int(k) for k in np.random.default_rng(24).integers(0, n, 34)]
+    for k, v in zip(ks, I.words_to_ints(c[ks])):
+        assert v == I.int_coeff(a, b, k), k
+    lo = c[:, 0].astype(np.uint64) | (c[:, 1].astype(np.uint64) << np.uint64(32))
+    hi = c[:, 2].astype(np.uint64)
+    got = ((hi % np.uint64(q)) * np.uint64((1 << 64) % q) + lo % np.uint64(q)) % np.uint64(q)
+    want = orc.polymul_tft(q, (a % q).astype(np.uint32), (b % q).astype(np.uint32), root=3)
+    assert np.array_equal(got.astype(np.uint32), want)
+
+
 def test_crt3_rejections(gpu):
     import torch
     from paper_1609_01010_gb300 import binding as B

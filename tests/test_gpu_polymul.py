@@ -167,9 +167,11 @@ def eval_at(c, r, p):
 
 
 @pytest.mark.parametrize("z", [1 << 22, 3000001])
-def test_workload3_largest_sampled(gpu, z):
-    """d+1 in {2^22, 3000001}: 64 coefficients by Definition 2 and 8 random
-    points c(r) = a(r) b(r) (false-pass probability <= n/p per point)."""
+def test_workload3_largest_full_oracle(gpu, orc, z):
+    """d+1 in {2^22, 3000001} (L = 2^23: the rows of 2^13 words, the only row
+    kernel that stages its inverse twiddles over the forward ones).  A fast
+    pre-check first (64 coefficients by Definition 2 and 8 random points
+    c(r) = a(r) b(r)), then every coefficient against the oracle."""
     p, a, b = W.workload3(z)
     c = gpu_product(p, a, b, gpu)
     n = len(c)
@@ -179,7 +181,18 @@ def test_workload3_largest_sampled(gpu, z):
     for _ in range(8):
         r = rng.randrange(1, p)
         assert eval_at(c, r, p) == eval_at(a, r, p) * eval_at(b, r, p) % p
-    assert int(c.max()) < p
+    want = orc.polymul_tft(p, a, b)
+    if not np.array_equal(c, want):
+        bad = np.flatnonzero(c != want)
+        raise AssertionError(f"z={z}: {len(bad)} mismatches, first at {bad[0]}")
+
+
+def test_unequal_lengths_at_2_23(gpu, orc):
+    """Unequal random operands whose product needs L = 2^23, both primes, in
+    full against the oracle (a permutation of inputs or rows would show)."""
+    rng = np.random.default_rng(23)
+    for p, z1, z2 in [(P1, 5000000, 1000003), (P2, 4194305, 2)]:
+        check(p, rnd(rng, z1, p), rnd(rng, z2, p), gpu, orc)
 
 
 @pytest.mark.parametrize("p", [P1, P2])
