@@ -10,11 +10,17 @@ each step's operands out of L2.  value = n / step time (coefficients/s).
 The same line also carries:
   e2e          the same product through polymul_mod_host (pinned host buffers,
                both copies inside the timed region);
-  roofline     the dominant kernel (row stage) against the integer-issue peak,
-               its duration taken with CUDA events over a profiled timed pass;
-  cpu_baseline the CPU oracle timed on a bounded sample on the host cores;
-  tft_vs_padded  degrees 3000 x 5000 mod 2013265921 (TFT length 8001) against
-               zero-padded NTTs of 8192 and 16384 (Eq. (12));
+  roofline     the dominant kernel (row stage) against the measured butterfly
+               peak of this GPU (polymul_probe_int), its duration taken with
+               CUDA events over a profiled timed pass;
+  cpu_baseline the CPU oracle timed on a bounded sample on all host cores (one
+               product per worker process) and on one core;
+  small_configs  workload 1 (full NTT 2048) and workload 2 (degrees 3000 x 5000
+               mod 2013265921, TFT length 8001, against zero-padded NTTs of 8192
+               and 16384, Eq. (12)): device time per product from CUDA-graph
+               replay, and the back-to-back call rate;
+  step_distribution  p10/p50/p90 of the headline product over 200 runs, cold
+               and warm L2;
   sweep        the large single products (d+1 in 2^16, 2^20, 2^22, 100000,
                1500000, 3000001): time, coeffs/s, compulsory-HBM fraction;
   crt3         exact integer products of 32-bit-coefficient operands (three
@@ -63,8 +69,7 @@ REF_BUDGET_S = 120.0
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, default cache
 # control, so L2 starts cold) on the sources whose digest is recorded here;
 # any later change to those sources makes the figure stale and it reads null.
-ROW_TRAFFIC = {"bytes": 50368000 + 8192, "sources_sha256_16": "e6e698fe18844d47",
-               "capture": "profiles/ncu_headline_kernels.md"}
+ROW_TRAFFIC = {"bytes": 50368000 + 8192, "sources_sha256_16": "e6e698fe18844d47"}
 ROW_SOURCES = ("device.cuh", "bodies.cuh", "k_large.cuh", "modarith.cuh", "internal.h")
 
 
@@ -193,8 +198,28 @@ def max_over_ranks(x, world, dev):
 
 
 # ---------------------------------------------------------------- CPU oracle
+def _oracle_product_worker(z):
+    """One headline-size product by the oracle in a worker process (spawned)."""
+    import oracle
+    from paper_1609_01010_gb300 import workloads as WW
+    p, a, b = WW.workload3(z)
+    t0 = time.perf_counter()
+    oracle.polymul_tft(p, a, b)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_oracle_rate(sample_products: int = 2):
-    """The oracle as it stands on one host core: coefficients/s on the headline workload."""
+    """The oracle as it stands on the host cores: coefficients/s on the
+    headline workload, on one core (products one after another) and on all
+    cores (one product per worker process, all at once)."""
+    import multiprocessing as mp
     import oracle
     p, a, b = W.workload3(HEAD_Z)
     n = len(a) + len(b) - 1
@@ -203,39 +228,63 @@ def cpu_oracle_rate(sample_products: int = 2):
     for _ in range(sample_products):
         oracle.polymul_tft(p, a, b)
     dt = (time.perf_counter() - t0) / sample_products
-    return {"value": n / dt, "unit": "coeffs/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample_products} full products of the headline workload (d+1 = 2^20 each, n = {n}), "
-                      f"recursive TFT/ITFT oracle, {dt:.2f} s per product"}
+    one = {"value": n / dt, "unit": "coeffs/s", "cores": 1, "kind": "oracle",
+           "sample": f"{sample_products} full products of the headline workload (d+1 = 2^20 each, n = {n}) one "
+                     f"after another on one core, recursive TFT/ITFT oracle, {dt:.2f} s per product"}
+    cores = host_cores()
+    # spawn: this process already holds a CUDA context, which forked workers must not inherit
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_product_worker, [1 << 10] * cores)  # start-up and library load, untimed
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_product_worker, [HEAD_Z] * cores)
+        wall = time.perf_counter() - t0
+    allc = {"value": cores * n / wall, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} full headline products at once, one per worker process on {cores} host cores "
+                      f"(os.sched_getaffinity), {wall:.2f} s wall, {statistics.median(per):.2f} s median per "
+                      f"product"}
+    out = dict(allc)
+    out["single_core"] = one
+    out["nproc"] = os.cpu_count()
+    return out
 
 
 def run_reference(args):
+    """The oracle on the host cores: each step is one round of `cores` full
+    headline products, one per worker process at once (the oracle itself is
+    sequential); value = products' coefficients / wall time."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    import oracle
+    import multiprocessing as mp
     p, a, b = W.workload3(HEAD_Z)
     n = len(a) + len(b) - 1
-    oracle.polymul_tft(p, a[:1024], b[:1024])
-    for _ in range(args.warmup):
-        oracle.polymul_tft(p, a[: 1 << 16], b[: 1 << 16])
-    # Each step is one full product (about 5 s on one core); steps stop after
-    # REF_BUDGET_S seconds so that any --steps finishes within a few minutes.
-    t0 = time.perf_counter()
-    done = 0
-    while done < args.steps and (done == 0 or time.perf_counter() - t0 < REF_BUDGET_S):
-        oracle.polymul_tft(p, a, b)
-        done += 1
-    dt = (time.perf_counter() - t0) / done
-    v = n / dt
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_product_worker, [1 << 10] * cores)
+        for _ in range(args.warmup):
+            pool.map(_oracle_product_worker, [1 << 14] * cores)
+        # Each step is one round of full products (several seconds); steps
+        # stop after REF_BUDGET_S seconds so that any --steps finishes within
+        # a few minutes.
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.steps and (done == 0 or time.perf_counter() - t0 < REF_BUDGET_S):
+            pool.map(_oracle_product_worker, [HEAD_Z] * cores)
+            done += 1
+        dt = (time.perf_counter() - t0) / done
+    v = cores * n / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "coeffs/s", "n_gpus": args.gpus,
             "steps": done, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"tft_polymul_p{p}_z{HEAD_Z}", "p": p, "z1": HEAD_Z, "z2": HEAD_Z, "n": n,
                        "L": 1 << 21, "impl": "CPU oracle (plain C, recursive TFT/ITFT, 64-bit %)"},
-            "cpu_baseline": {"value": v, "unit": "coeffs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{done} of {args.steps} requested full products timed (budget "
-                                       f"{REF_BUDGET_S:.0f} s) after {args.warmup} warm-up products of "
-                                       f"2^16-coefficient operands"},
+            "cpu_baseline": {"value": v, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{done} of {args.steps} requested rounds timed (budget "
+                                       f"{REF_BUDGET_S:.0f} s), each round {cores} full headline products at "
+                                       f"once, one per worker process, after {args.warmup} warm-up rounds of "
+                                       f"2^14-coefficient operands"},
             "e2e": {"value": v, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -282,7 +331,36 @@ def headline(args, dev, stream, B, world):
         barrier(world)
         # correctness of the timed outputs (sampled against Definition 2)
         got = host_u32(Cm[(args.steps - 1) % sets])
-    return p, z, n, ms, got, a, b, step
+    return p, z, n, ms, got, a, b, step, ptrs
+
+
+def step_distribution(stream, B, p, z, ptrs, reps=200):
+    """Per-product device time (CUDA events around each product) over `reps`
+    products: cold L2 (the 16 rotating buffer sets, 400 MB, each product's
+    operands evicted by the others) and warm L2 (one set, 25 MB, resident).
+    An event between two products keeps the next product's first kernel from
+    starting under the previous one's last (programmatic dependent launch), so
+    these times are slightly above the back-to-back mean of the headline."""
+    import torch
+    sh = stream.cuda_stream
+    sets = len(ptrs)
+    out = {}
+    for name, pick in (("cold_l2", lambda i: ptrs[i % sets]), ("warm_l2", lambda i: ptrs[0])):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            for i in range(10):
+                pa, pb, pc = pick(i)
+                B.polymul_mod_async(p, pa, z - 1, pb, z - 1, pc, sh)
+            for i in range(reps):
+                pa, pb, pc = pick(i)
+                evs[i][0].record(stream)
+                B.polymul_mod_async(p, pa, z - 1, pb, z - 1, pc, sh)
+                evs[i][1].record(stream)
+            stream.synchronize()
+        us = np.array([a.elapsed_time(b) * 1e3 for a, b in evs])
+        out[name] = {"p10_us": float(np.percentile(us, 10)), "p50_us": float(np.percentile(us, 50)),
+                     "p90_us": float(np.percentile(us, 90)), "mean_us": float(us.mean()), "runs": reps}
+    return out
 
 
 def profiled_pass(args, stream, step):
@@ -298,25 +376,50 @@ def profiled_pass(args, stream, step):
     return ms, cnt
 
 
-def e2e_pass(args, p, a, b):
+def e2e_pass(args, p, a, b, streams=3):
+    """End to end from pinned host buffers through the public API: each step
+    copies its operands in, computes and copies its product back
+    (polymul_mod_host_async); steps rotate over `streams` streams with their
+    own buffer sets, so one step's host-link copies run while another
+    computes.  Wall-clock time from the first call to the last stream's end.
+    Beside it, the synchronous polymul_mod_host latency of one product."""
     import torch
     from paper_1609_01010_gb300 import binding as B
     z = len(a)
     n = 2 * z - 1
-    ha = torch.from_numpy(a.view(np.int32)).pin_memory()
-    hb = torch.from_numpy(b.view(np.int32)).pin_memory()
-    hc = torch.empty(n, dtype=torch.int32).pin_memory()
-    for _ in range(3):
-        B.polymul_mod_host(p, ha.data_ptr(), z - 1, hb.data_ptr(), z - 1, hc.data_ptr())
-    reps = max(3, min(args.steps, 50))
+    sets = []
+    for _ in range(streams):
+        ha = torch.from_numpy(a.view(np.int32)).pin_memory()
+        hb = torch.from_numpy(b.view(np.int32)).pin_memory()
+        hc = torch.empty(n, dtype=torch.int32).pin_memory()
+        # the tensors stay referenced: freed pinned memory would be handed to the next set
+        sets.append((torch.cuda.Stream(), ha.data_ptr(), hb.data_ptr(), hc, hc.data_ptr(), ha, hb))
+    L = B.lib()
+
+    def run(k):
+        for i in range(k):
+            st, pa, pb, _, pc = sets[i % streams][:5]
+            assert L.polymul_mod_host_async(p, pa, z - 1, pb, z - 1, pc, st.cuda_stream) == 0
+        for st, *_ in sets:
+            st.synchronize()
+    run(2 * streams)
+    reps = max(3 * streams, min(args.steps, 60))
     t0 = time.perf_counter()
-    for _ in range(reps):
-        B.polymul_mod_host(p, ha.data_ptr(), z - 1, hb.data_ptr(), z - 1, hc.data_ptr())
+    run(reps)
     dt = (time.perf_counter() - t0) / reps
+    ok = sampled_ok(sets[(reps - 1) % streams][3].numpy().view(np.uint32), a, b, p, [0, n // 2, n - 1])
+    for _ in range(3):
+        L.polymul_mod_host(p, sets[0][1], z - 1, sets[0][2], z - 1, sets[0][4])
+    t0 = time.perf_counter()
+    for _ in range(10):
+        L.polymul_mod_host(p, sets[0][1], z - 1, sets[0][2], z - 1, sets[0][4])
+    lat = (time.perf_counter() - t0) / 10
     return {"value": n / dt, "unit": "coeffs/s", "h2d_bytes_per_step": 8 * z, "d2h_bytes_per_step": 4 * n,
-            "ms_per_step": dt * 1e3, "steps": reps, "api": "polymul_mod_host (pinned host buffers; at this size staged through device memory by "
-                   "copy kernels over the host link where the device walks the host page tables, else by "
-                   "copy engines)"}
+            "ms_per_step": dt * 1e3, "steps": reps, "streams": streams, "correct_sampled": bool(ok),
+            "sync_latency_ms": lat * 1e3,
+            "api": "polymul_mod_host_async on pinned host buffers (copy engines in and out, staged through a "
+                   "stream-ordered device buffer), steps rotating over the streams; sync_latency_ms: one "
+                   "polymul_mod_host call alone"}
 
 
 def sampled_ok(c, a, b, p, ks):
@@ -331,28 +434,69 @@ def sampled_ok(c, a, b, p, ks):
     return True
 
 
-def tft_vs_padded(dev, stream, B):
+def graph_device_us(call, stream, per_graph=200, replays=10):
+    """Device time per call: `per_graph` calls captured into one CUDA graph
+    (through the public C ABI) and replayed; no host launch cost inside."""
     import torch
-    p, a, b = W.workload2()
-    n = len(a) + len(b) - 1
-    da, db = dev_u32(a, dev), dev_u32(b, dev)
-    dc = torch.empty(n, dtype=torch.int32, device=dev)
-    sh = stream.cuda_stream
-    out = {"workload": "degrees 3000 x 5000 mod 2013265921, n = 8001", "p": p, "n": n}
     with torch.cuda.stream(stream):
-        for name, Lp in (("tft_8192", None), ("padded_ntt_8192", 8192), ("padded_ntt_16384", 16384)):
-            def f(i, Lp=Lp):
-                if Lp:
-                    B.polymul_mod_padded_async(p, da, len(a) - 1, db, len(b) - 1, dc, Lp, sh)
-                else:
-                    B.polymul_mod_async(p, da, len(a) - 1, db, len(b) - 1, dc, sh)
-            for i in range(20):
-                f(i)
-            out[name + "_us"] = ev_time(f, 500, stream) * 1e3
-    out["speedup_vs_padded_16384"] = out["padded_ntt_16384_us"] / out["tft_8192_us"]
-    out["speedup_vs_padded_8192"] = out["padded_ntt_8192_us"] / out["tft_8192_us"]
-    out["note"] = ("latency of one product per call (three kernels each), "
-                   "CUDA events over 500 back-to-back calls")
+        for _ in range(5):
+            call()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(per_graph):
+                call()
+        g.replay()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(replays):
+            g.replay()
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / (per_graph * replays) * 1e3
+
+
+def small_configs(dev, stream, B):
+    """Workloads 1 and 2: degree-1023 operands (full NTT 2048) and degrees
+    3000 x 5000 mod 2013265921 (TFT length 8001) against the zero-padded
+    NTTs of 8192 and 16384 (Eq. (12)).  Per product: the back-to-back call
+    rate from one host thread (host launch cost included) and the device
+    time from CUDA-graph replay."""
+    import torch
+    L = B.lib()
+    sh = stream.cuda_stream
+    out = {}
+    for wname, (p, a, b) in (("workload1_ntt2048", W.workload1()), ("workload2_tft8001", W.workload2())):
+        n = len(a) + len(b) - 1
+        da, db = dev_u32(a, dev), dev_u32(b, dev)
+        dc = torch.empty(n, dtype=torch.int32, device=dev)
+        pa, pb, pc = da.data_ptr(), db.data_ptr(), dc.data_ptr()
+        cases = [("tft", None)] if wname.startswith("workload1") else [("tft", None), ("padded_ntt_8192", 8192),
+                                                                          ("padded_ntt_16384", 16384)]
+        res = {"p": p, "n": n, "z1": len(a), "z2": len(b)}
+        for name, Lp in cases:
+            if Lp:
+                def call(Lp=Lp):
+                    assert L.polymul_mod_padded_async(p, pa, len(a) - 1, pb, len(b) - 1, pc, Lp, sh) == 0
+            else:
+                def call():
+                    assert L.polymul_mod_async(p, pa, len(a) - 1, pb, len(b) - 1, pc, sh) == 0
+            with torch.cuda.stream(stream):
+                for _ in range(20):
+                    call()
+                rate_us = ev_time(lambda i: call(), 500, stream) * 1e3
+            res[name] = {"device_us": graph_device_us(call, stream), "call_rate_us": rate_us}
+        want = sampled_ok(host_u32(dc), a, b, p, [0, n // 2, n - 1])
+        res["correct_sampled"] = bool(want)
+        if "padded_ntt_16384" in res:
+            res["device_speedup_vs_padded_16384"] = res["padded_ntt_16384"]["device_us"] / res["tft"]["device_us"]
+            res["device_speedup_vs_padded_8192"] = res["padded_ntt_8192"]["device_us"] / res["tft"]["device_us"]
+        out[wname] = res
+    out["note"] = ("device_us: CUDA graph of 200 calls through the C ABI, replayed (device time per product); "
+                   "call_rate_us: 500 back-to-back calls from one host thread, CUDA events (bounded by the host "
+                   "launch cost at these sizes)")
     return out
 
 
@@ -579,6 +723,18 @@ def serve_run(dev, B, mode, t_arr, prime, da_, db_, pools, budget, check_every=9
         B.polymul_server_wait(srv, t, 120000)
     t_all = time.perf_counter() - t0
     stats = B.polymul_server_stats(srv)
+    # per size class: small requests (L <= 2^17, the ones the serving form
+    # batches and runs on its high-priority lane) and large ones
+    lat = np.array([B.polymul_server_latency(srv, t) for t in tickets])
+    n_req = da_[:len(tickets)].astype(np.int64) + db_[:len(tickets)].astype(np.int64) + 1
+    small = np.ceil(np.log2(n_req)) <= 17
+    classes = {}
+    for name, mask in (("small_L_le_2^17", small), ("large", ~small)):
+        v = lat[mask]
+        if len(v):
+            classes[name] = {"requests": int(len(v)), "p50_us": float(np.percentile(v, 50)),
+                             "p99_us": float(np.percentile(v, 99)), "max_us": float(v.max())}
+    stats["classes"] = classes
     B.polymul_server_destroy(srv)
     del arena
     return stats, t_sub, t_all, checks
@@ -610,7 +766,8 @@ def serving(dev, B, seconds, rate=20000.0, budget=8 << 30, burst=20000):
         stats, t_sub, t_all, checks = serve_run(dev, B, mode, t_arr, prime, da_, db_, pools, budget)
         out[name] = {"p50_us": stats["p50_us"], "p90_us": stats["p90_us"], "p99_us": stats["p99_us"],
                      "max_us": stats["max_us"], "mean_us": stats["mean_us"], "submit_s": t_sub, "drain_s": t_all,
-                     "throughput_req_per_s": len(t_arr) / t_all, "coeffs_per_s": n_total / t_all}
+                     "throughput_req_per_s": len(t_arr) / t_all, "coeffs_per_s": n_total / t_all,
+                     "classes": stats["classes"]}
         for q, offa, za, offb, zb, pc in checks[:3]:
             want = oracle.polymul_tft(q, pool_host[q][offa:offa + za], pool_host[q][offb:offb + zb])
             ok = ok and bool(np.array_equal(host_u32(pc), want))
@@ -642,7 +799,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load before the timed region")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--schedule", action="append", default=[], metavar="L:SIGMA:C",
+                    help="use rows of 2^SIGMA words and column tiles of C words for transform length 2^L "
+                         "(repeatable; default: the library's tuned table)")
     ap.add_argument("--skip", default="",
                     help="comma list of parts to skip: e2e,cpu,padded,sweep,crt3,fig3,radix,batched,serving")
     args = ap.parse_args()
@@ -661,12 +821,27 @@ def main():
     from paper_1609_01010_gb300 import binding as B
     B.lib()
     skip = set(x for x in args.skip.split(",") if x)
+    if args.schedule:
+        import tempfile
+        rows = []
+        for spec in args.schedule:
+            l_, sg_, c_ = (int(x) for x in spec.split(":"))
+            rows.append({"l": l_, "sigma": sg_, "C": c_, "us": 0.0})
+        with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
+            json.dump({"device": "bench --schedule", "p": 0, "schedules": rows}, f)
+        B.polymul_load_schedules(f.name)
+        os.unlink(f.name)
     peaks, peak_src = load_peaks()
     stream = torch.cuda.Stream(device=dev)
 
+    int_peaks = {}
+    for kind, name in B.PROBE_KINDS.items():
+        ops, pms = B.polymul_probe_int(kind, 1 << 15)
+        int_peaks[name] = {"per_s": ops, "ms": pms}
     with ClockSampler(local) as clk:
-        p, z, n, ms, got, a, b, step = headline(args, dev, stream, B, world)
+        p, z, n, ms, got, a, b, step, ptrs = headline(args, dev, stream, B, world)
         prof_ms, prof_cnt = profiled_pass(args, stream, step)
+        dist = step_distribution(stream, B, p, z, ptrs)
     ms = max_over_ranks(ms, world, dev)
     ks = [0, 1, n // 3, n // 2, n - 1] + list(np.random.default_rng(1).integers(0, n, 27))
     correct = sampled_ok(got, a, b, p, [int(k) for k in ks])
@@ -683,15 +858,23 @@ def main():
     row_ms = prof_ms[2] / max(1, prof_cnt[2])
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_tops = sm_count * 4 * 32 * sm_mhz * 1e6 / 1e12
+    issue_tops = sm_count * 4 * 32 * sm_mhz * 1e6 / 1e12
+    # measured peak: the butterfly probe (the kernels' own butterfly, register
+    # only, full occupancy) in butterflies/s, times the 7 ops a butterfly counts
+    peak_tops = int_peaks["forward butterfly"]["per_s"] * ops_per_bfly / 1e12
     achieved = ops_per_launch / (row_ms * 1e-3) / 1e12 if row_ms > 0 else None
     total_prof = sum(prof_ms[1:4])
     roofline = {"bound": "alu", "kernel": "k_row_fused (row stage: forward x2, pointwise, inverse)",
                 "achieved": achieved, "peak": peak_tops, "unit": "Tintop/s",
                 "frac": (achieved / peak_tops) if achieved else None,
                 "traffic": row_kernel_traffic(),
-                "peak_source": f"{sm_count} SMs x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz (1 warp-instruction "
-                               "issue per SMSP per clock; MEASURED_PEAKS sm_max_mhz)",
+                "peak_source": "measured on this GPU by polymul_probe_int kind 0 (the lazy forward butterfly of "
+                               "the transform kernels, 16 independent register chains per thread, full occupancy): "
+                               f"{int_peaks['forward butterfly']['per_s'] / 1e12:.3f} T butterflies/s x 7 ops",
+                "issue_ceiling": {"value": issue_tops, "unit": "Tintop/s",
+                                  "derivation": f"{sm_count} SMs x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz (one "
+                                                "warp-instruction issue per SMSP per clock)"},
+                "int_peaks": int_peaks,
                 "algorithmic_ops_per_launch": ops_per_launch,
                 "row_stage_us_per_launch": row_ms * 1e3,
                 "kernel_share_of_step": {"col_tft": prof_ms[1] / total_prof if total_prof else None,
@@ -710,7 +893,7 @@ def main():
     roofline["product"] = {"algorithmic_ops": prod_ops, "achieved": prod_ops / (ms * 1e-3) / 1e12,
                            "frac": prod_ops / (ms * 1e-3) / 1e12 / peak_tops,
                            "note": "all three kernels' butterflies (7 ops) and pointwise products (11 ops) "
-                                   "per step time, against the same integer-issue peak"}
+                                   "per step time, against the same measured peak"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     comp_bytes = 4 * (2 * z + n)
     line = {"metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
@@ -723,13 +906,13 @@ def main():
             "hbm_compulsory": {"bytes_per_step": comp_bytes, "gbs": comp_bytes / (ms * 1e-3) / 1e9,
                                "peak_gbs": hbm, "frac": comp_bytes / (ms * 1e-3) / 1e9 / hbm,
                                "peak_source": peak_src},
-            "roofline": roofline, "gpu_launches": 3 * args.steps,
+            "roofline": roofline, "gpu_launches": 3 * args.steps, "step_distribution": dist,
             "clocks": clk.summary()}
     if rank == 0:
         if "e2e" not in skip:
             line["e2e"] = e2e_pass(args, p, a, b)
         if "padded" not in skip:
-            line["tft_vs_padded"] = tft_vs_padded(dev, stream, B)
+            line["small_configs"] = small_configs(dev, stream, B)
         if "sweep" not in skip:
             line["sweep"] = sweep(dev, stream, B, peaks)
         if "crt3" not in skip:

@@ -53,6 +53,8 @@ extern "C" {
 #define POLY_EINVAL (-7)       /* a size or argument is out of range */
 #define POLY_EBUSY (-8)        /* request larger than the server's memory budget */
 #define POLY_ENOTFOUND (-9)    /* unknown server ticket */
+#define POLY_EINVAL_COEF (-10) /* a validating call found an input coefficient outside [0, p) */
+#define POLY_EDEBUG_CHECK (-11) /* debug build only: a range or index check inside a kernel failed */
 
 #define POLY_MAX_LOG_L 24
 
@@ -61,6 +63,35 @@ const char *polymul_strerror(int status);
 
 /* Text of the last failing CUDA call made by this thread ("" if none). */
 const char *polymul_last_error(void);
+
+/*
+ * The device status word of the current device: POLY_OK, or the first error
+ * a kernel recorded since it was last cleared.  POLY_ETIMEOUT: a bounded
+ * wait inside a kernel expired (that kernel skipped the work whose data
+ * never arrived, so its output is not valid).  POLY_EDEBUG_CHECK: a range
+ * or index check of the debug build (libpolymul_debug.so, built with
+ * python -m paper_1609_01010_gb300.build --debug) failed -- a residue a
+ * kernel stored outside its stated range, or an index outside its buffer.
+ * clear != 0 resets it to POLY_OK after reading.  Synchronous (a
+ * device-to-host copy on the legacy default stream).  POLY_ECUDA if the
+ * word cannot be read.
+ */
+int polymul_device_status(int clear);
+
+/*
+ * Validation mode (off by default).  While on, every entry point that takes
+ * modular operands -- polymul_mod[_async], polymul_mod_padded_async,
+ * polymul_mod_host, polymul_cyclic_async, polymul_negacyclic_async,
+ * polymul_mod_radix_async, polymul_batch_exec[_nograph],
+ * polymul_mod_batched[_plain] and polymul_server_submit -- first checks with
+ * one pass over a and b that every coefficient lies in [0, p), and returns
+ * POLY_EINVAL_COEF (computing nothing, c untouched) if one does not.  The
+ * check synchronises the caller's stream (the server's submit: the legacy
+ * default stream), so it is meant for debugging and for callers whose inputs
+ * are untrusted.  polymul_mod_noalloc_async and polymul_crt3_async (whose
+ * inputs are arbitrary 32-bit words) are never checked.  Process-wide.
+ */
+int polymul_set_validate(int on);
 
 /* Library version string. */
 const char *polymul_version(void);
@@ -89,11 +120,23 @@ int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const ui
  * Synchronous, on an internal stream.  Where the device walks the host's
  * page tables (address translation services; GB300 with a Grace host, over
  * NVLink-C2C), products with da+db+1 <= 2^19 are computed on the host
- * buffers in place and larger ones are staged through device memory by
- * copy kernels on all SMs; elsewhere the copy engines stage them (pinned
- * memory gives the best rate).
+ * buffers in place.  Larger ones are staged through a stream-ordered device
+ * buffer: pinned buffers by the copy engines, pageable ones by copy kernels
+ * on all SMs where the device can address them, else by the runtime's
+ * staged copies.
  */
 int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c);
+
+/*
+ * The host-buffer product enqueued on `stream` without waiting: the same
+ * paths as polymul_mod_host.  a and b must stay valid and unchanged, and c
+ * untouched, until the stream has passed this call's work (synchronise the
+ * stream or an event recorded after the call).  A caller with many products
+ * spreads them over a few streams so that one product's host-link copies run
+ * while another computes.
+ */
+int polymul_mod_host_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                           void *stream);
 
 /*
  * Allocation-free product for callers that cannot let a library allocate
@@ -108,8 +151,11 @@ int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *
  * path's workspace is a 1 MiB static device array inside the library (and the
  * twiddle tables and step lists it needs are static arrays too: about 5.5 MiB
  * in total, held by every GPU that loads the library until the process
- * exits).  This call never calls cudaMalloc, cudaFree or any other
- * allocating routine.
+ * exits).  This call makes no device allocation: it never calls
+ * cudaMalloc, cudaMallocAsync, cudaFree or a library routine that allocates
+ * device memory.  (Its first call on a device fills small host-side lookup
+ * tables; that is ordinary host memory.)  It records no profile events
+ * (polymul_profile_begin/end do not see its kernels).
  *  - p must be 469762049 or 2013265921 (else POLY_EINVAL_PRIME).
  *  - n = da+db+1 must not exceed 131072 = 2^17 (else POLY_ETOO_LONG).
  *  - The first call on a device sets the static tables up (with that device
@@ -125,7 +171,8 @@ int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const u
 
 /*
  * Measurement helpers.  Between polymul_profile_begin and polymul_profile_end
- * every single-product call records CUDA events around its kernels on its
+ * every single-product call (except polymul_mod_noalloc_async) records CUDA
+ * events around its kernels on its
  * stream.  polymul_profile_end synchronises those events and returns the
  * summed device time in milliseconds and the number of launches per kernel:
  * index 0 the one-CTA product kernel (L <= 512), 1 the TFT column stage,
@@ -133,6 +180,21 @@ int polymul_mod_noalloc_async(uint32_t p, const uint32_t *a, int64_t da, const u
  */
 int polymul_profile_begin(void);
 int polymul_profile_end(double *ms4, int64_t *launches4);
+
+/*
+ * Measured integer-pipe peak of the current device (a diagnostic with no
+ * counterpart in the paper: the denominator of the transform kernels'
+ * roofline).  Runs one probe kernel of `iters` loop iterations at full
+ * occupancy: 16 independent register accumulators per thread, no memory
+ * traffic in the loop.  kind 0: the lazy forward butterfly (the transform
+ * kernels' instruction mix, 3 multiplies per butterfly); 1: the lazy inverse
+ * butterfly; 2: mul.lo.u32; 3: mul.hi.u32; 4: add.u32; 5: min.u32.
+ * *ops_per_s: butterflies per second (kinds 0, 1) or instructions per second
+ * (2..5), from CUDA events around the timed launch (after one warm-up
+ * launch); *ms: that launch's duration.  Allocates and frees a small output
+ * buffer.  POLY_EINVAL for an unknown kind or iters outside [1, 2^24].
+ */
+int polymul_probe_int(int kind, int iters, double *ops_per_s, double *ms);
 
 /*
  * Cyclic convolution: c = a * b mod (x^N - 1), c_k = sum over i + j = k mod N
@@ -149,7 +211,12 @@ int polymul_cyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32
 /*
  * Negacyclic convolution: c = a * b mod (x^N + 1) (x^N = -1), the second
  * factor of Eq. 13's splitting of x^{2N} - 1.  Arguments as
- * polymul_cyclic_async; computed as the linear product folded with a sign.
+ * polymul_cyclic_async.  A power-of-two N >= 512 with 2N dividing p - 1 runs
+ * as a twisted cyclic convolution of length N: a_i and b_i times psi^i (psi a
+ * primitive 2N-th root of unity, so x = psi y maps x^N + 1 to -(y^N - 1)),
+ * the length-N transform product, and the result times psi^-i (a transient
+ * workspace of za + zb words from the stream-ordered pool).  Any other N
+ * computes the linear product and folds it with a sign.
  */
 int polymul_negacyclic_async(uint32_t p, const uint32_t *a, int64_t za, const uint32_t *b, int64_t zb,
                              uint32_t *c, int64_t N, void *stream);
@@ -226,8 +293,13 @@ typedef struct polymul_batch polymul_batch;
  * operand i of a occupies a[a_off[i] .. a_off[i+1]) (length = degree+1 >= 1),
  * likewise b with b_off, and product i is written to c[c_off[i] ..
  * c_off[i] + len_a + len_b - 1).  The offset arrays are HOST arrays of
- * count+1 int64 entries; the plan copies them.  Schedules per size class come
- * from the autotuned table (polymul_autotune) or the built-in defaults.
+ * count+1 int64 entries; the plan copies them.  A product with L <= 8192 is
+ * one work item; a longer one is split into column, row and ITFT items with
+ * rows of 2^12 words (one 256-thread CTA per row, fixed by the kernel's CTA
+ * shape) and column tiles of the width its size class (log2 L) has in the
+ * tuned table -- polymul_autotune times a batch of each length at every
+ * width, polymul_load_schedules reads it back ("batch_C") -- or, untuned, a
+ * built-in rule (polymul_get_batch_width).
  */
 int polymul_batch_create(uint32_t p, int64_t count, const int64_t *a_off, const int64_t *b_off,
                          const int64_t *c_off, polymul_batch **out);
@@ -277,10 +349,12 @@ int polymul_mod_batched_plain(uint32_t p, int64_t count, const uint32_t *a, cons
 
 /* ---------------------------------------------------------------- autotuner */
 /*
- * Time the candidate schedules (row block, column tile, threads) for every
+ * Time the candidate schedules (row block, column tile) for every
  * transform length 2^lo_log .. 2^hi_log on the current device and prime p,
- * keep the fastest per length, and write the table as JSON to `json_path`
- * (NULL: keep in memory only).  Subsequent plans use the table.
+ * and the batched kernel's column-tile widths for the lengths a batch splits
+ * into items (2^14 .. 2^22), keep the fastest per length, and write the
+ * table as JSON to `json_path` (NULL: keep in memory only).  Subsequent
+ * plans use the table.
  */
 int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path);
 
@@ -295,22 +369,36 @@ int polymul_load_schedules(const char *json_path);
  */
 int polymul_get_schedule(int l, int *sigma, int *C);
 
+/*
+ * Column-tile width (8, 32 or 128 words) of a product of length L = 2^l
+ * inside a batch (l in 14..22): tuned or built-in.  POLY_EINVAL outside that
+ * range.
+ */
+int polymul_get_batch_width(int l, int *C);
+
 /* ---------------------------------------------------------------- serving */
 typedef struct polymul_server polymul_server;
 
 /* Dispatch modes of the server. */
-#define POLY_SERVE_BATCH 0 /* a group's requests with L <= 2^17 (8 or more) as one persistent batched launch, the rest plain */
+#define POLY_SERVE_BATCH 0 /* serving form: small requests (L <= 2^17) on a high-priority lane, batched in one persistent launch when 2 or more, the rest plain */
 #define POLY_SERVE_PLAIN 1 /* every request as its own plain product (the comparator) */
 
 /*
  * A continuous-batching server on the current device (the paper has no
  * serving layer).  Requests are admitted while the bytes they hold (inputs,
  * output and workspace) fit in mem_budget_bytes; the rest wait in arrival
- * order.  A free stream (of `n_streams`) takes all admissible queued requests
+ * order.  A free stream (of `n_streams`) takes admissible queued requests
  * of one prime as a group and runs them as `mode` says, so work admitted while
- * other work runs overlaps on the GPU.  Twiddle tables and plans for
- * 469762049 and 2013265921 are made resident at creation.  POLY_EINVAL for a
- * zero budget, n_streams outside [1, 64] or an unknown mode.
+ * other work runs overlaps on the GPU.  In POLY_SERVE_BATCH one stream in four
+ * (at least one) is a high-priority lane for small requests (L <= 2^17); the
+ * others take large requests first.  A scheduler thread polls the groups'
+ * completion events (spinning while work is in flight or arrived within the
+ * last 2 ms, so it holds a host core busy meanwhile).  Twiddle tables and plans for
+ * 469762049 and 2013265921 are made resident at creation, every kernel a
+ * request can meet is loaded by running zero-input products of every length
+ * on the device, and the stream-ordered pool is grown to min(budget, 1 GiB)
+ * (creation takes some tens of milliseconds).  POLY_EINVAL for a zero budget,
+ * n_streams outside [1, 64] or an unknown mode.
  */
 int polymul_server_create(size_t mem_budget_bytes, int n_streams, int mode, polymul_server **out);
 
@@ -333,6 +421,10 @@ int polymul_server_wait(polymul_server *srv, uint64_t ticket, int64_t timeout_ms
  * microseconds: out[0..5] = {count, p50, p90, p99, max, mean}.
  */
 int polymul_server_stats(polymul_server *srv, double *out6);
+
+/* Latency (submit -> completion seen by the server, microseconds) of one done
+ * ticket; POLY_EINVAL while it is not done, POLY_ENOTFOUND for an unknown one. */
+int polymul_server_latency(polymul_server *srv, uint64_t ticket, double *us);
 
 int polymul_server_destroy(polymul_server *srv);
 

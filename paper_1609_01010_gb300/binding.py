@@ -14,7 +14,10 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpolymul.so")
+# POLYMUL_DEBUG_LIB=1 loads the debug build (range and index checks inside
+# the kernels, reported by polymul_device_status) instead of the release one.
+LIB_PATH = os.path.join(_HERE, "libpolymul_debug.so" if os.environ.get("POLYMUL_DEBUG_LIB") == "1"
+                        else "libpolymul.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -36,10 +39,12 @@ _SIGS = {
     "polymul_version": (ctypes.c_char_p, []),
     "polymul_last_error": (ctypes.c_char_p, []),
     "polymul_device_status": (ctypes.c_int, [ctypes.c_int]),
+    "polymul_set_validate": (ctypes.c_int, [ctypes.c_int]),
     "polymul_mod": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
     "polymul_mod_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_mod_padded_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, i64, vp]),
     "polymul_mod_host": (ctypes.c_int, [u32, vp, i64, vp, i64, vp]),
+    "polymul_mod_host_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_mod_noalloc_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, vp]),
     "polymul_profile_begin": (ctypes.c_int, []),
     "polymul_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), I64P]),
@@ -65,12 +70,14 @@ _SIGS = {
     "polymul_crt3_async": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
     "polymul_mod_radix_async": (ctypes.c_int, [u32, vp, i64, vp, i64, vp, ctypes.c_int, vp]),
     "polymul_get_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "polymul_get_batch_width": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
     "polymul_server_submit": (ctypes.c_int, [vp, u32, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]),
     "polymul_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     "polymul_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, i64]),
     "polymul_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
     "polymul_server_destroy": (ctypes.c_int, [vp]),
+    "polymul_server_latency": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -94,6 +101,11 @@ def lib():
 def polymul_device_status(clear: bool = False) -> int:
     """The current device's status word (0, POLY_ETIMEOUT or POLY_EINVAL_COEF)."""
     return int(lib().polymul_device_status(1 if clear else 0))
+
+
+def polymul_set_validate(on: bool) -> None:
+    """Validation mode: entry points check their inputs are below p first."""
+    _check(lib().polymul_set_validate(1 if on else 0), "polymul_set_validate")
 
 
 def strerror(status: int) -> str:
@@ -159,6 +171,12 @@ def polymul_mod_noalloc_async(p: int, a, da: int, b, db: int, c, stream=None) ->
 def polymul_mod_host(p: int, a, da: int, b, db: int, c) -> None:
     """Host buffers (numpy uint32 arrays or pinned torch CPU tensors)."""
     _check(lib().polymul_mod_host(p, _ptr(a), da, _ptr(b), db, _ptr(c)), "polymul_mod_host")
+
+
+def polymul_mod_host_async(p: int, a, da: int, b, db: int, c, stream=None) -> None:
+    """Host buffers, enqueued on `stream`; they must stay valid until the stream passes the call."""
+    _check(lib().polymul_mod_host_async(p, _ptr(a), da, _ptr(b), db, _ptr(c), _stream(stream)),
+           "polymul_mod_host_async")
 
 
 def polymul_profile_begin() -> None:
@@ -315,6 +333,13 @@ def polymul_mod_radix_async(p: int, a, da: int, b, db: int, c, m: int, stream=No
            "polymul_mod_radix_async")
 
 
+def polymul_get_batch_width(l: int) -> int:
+    """Column-tile width of a length-2^l product inside a batch."""
+    c = ctypes.c_int()
+    _check(lib().polymul_get_batch_width(l, ctypes.byref(c)), "polymul_get_batch_width")
+    return c.value
+
+
 def polymul_get_schedule(l: int) -> tuple[int, int]:
     """(sigma, C) of the three-kernel path for L = 2^l."""
     sg, c = ctypes.c_int(), ctypes.c_int()
@@ -346,6 +371,13 @@ def polymul_server_poll(srv: int, ticket: int) -> bool:
 
 def polymul_server_wait(srv: int, ticket: int, timeout_ms: int = 60000) -> None:
     _check(lib().polymul_server_wait(srv, ticket, timeout_ms), "polymul_server_wait")
+
+
+def polymul_server_latency(srv: int, ticket: int) -> float:
+    """Microseconds from submit to completion of a done ticket."""
+    us = ctypes.c_double()
+    _check(lib().polymul_server_latency(srv, ticket, ctypes.byref(us)), "polymul_server_latency")
+    return us.value
 
 
 def polymul_server_stats(srv: int) -> dict:

@@ -2,8 +2,10 @@
 
 Each translation unit under csrc/ is compiled in parallel to _build/*.o and
 linked into paper_1609_01010_gb300/libpolymul.so (CUDA runtime linked
-statically).  Rebuilds only what changed.  Usage: python -m
-paper_1609_01010_gb300.build [--force].
+statically).  Rebuilds only what changed.  With --debug it builds
+libpolymul_debug.so instead (objects in _build_debug/): the kernels'
+range and index checks compiled in.  Usage: python -m
+paper_1609_01010_gb300.build [--force] [--debug].
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpolymul.so")
+LIB_DEBUG = os.path.join(PKG, "libpolymul_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -61,8 +64,14 @@ def _variants() -> dict[str, list[tuple[str, list[str]]]]:
     return {"k_cols.cu": cols, "k_cols_tma.cu": tcols}
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Builds libpolymul.so, or with debug=True libpolymul_debug.so: the same
+    library with the kernels' range and index checks compiled in
+    (PM_DEBUG_CHECKS; failures land in the device status word)."""
+    build_dir = BUILD + ("_debug" if debug else "")
+    lib_path = LIB_DEBUG if debug else LIB
+    extra = ["-DPM_DEBUG_CHECKS=1"] if debug else []
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
     cc = nvcc()
@@ -72,10 +81,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in srcs:
         base = os.path.basename(src)[:-3]
         for tag, defs in variants.get(os.path.basename(src), [(None, [])]):
-            obj = os.path.join(BUILD, base + (f".{tag}" if tag else "") + ".o")
+            obj = os.path.join(build_dir, base + (f".{tag}" if tag else "") + ".o")
             objs.append(obj)
             if force or _stale(obj, [src] + deps):
-                jobs.append([cc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj])
+                jobs.append([cc, *ARCH, *FLAGS, *extra, *defs, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
@@ -84,16 +93,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed ({r.returncode}): {' '.join(cmd)}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError(f"link failed: {' '.join(cmd)}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -30,7 +30,7 @@ namespace pm {
 // Size the work list of `count` products.  `ptr_a/b/c[i]` are byte offsets
 // (from the exec-time base pointers) of product i's operands and output.
 int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_t *zb, const uint64_t *a_off,
-                   const uint64_t *b_off, const uint64_t *c_off, int C, std::vector<BatchDesc> &descs,
+                   const uint64_t *b_off, const uint64_t *c_off, std::vector<BatchDesc> &descs,
                    std::vector<WorkItem> &items, uint64_t *ws_bytes, size_t *smem_bytes) {
     descs.assign(count, BatchDesc{});
     items.clear();
@@ -60,11 +60,13 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
             small.push_back({d.n, i});
         } else {
             if (l - BATCH_SIGMA > LARGE_MAX_LOG_T) return POLY_ETOO_LONG;
+            const int C = batch_width_for(l);
             Schedule sch{BATCH_SIGMA, C};
             LargeDesc ld;
             int rc = prepare_large(ctx, nullptr, d.za, nullptr, d.zb, nullptr, l, true, sch, &ld);
             if (rc) return rc;
             d.large = 1;
+            d.C = C;
             d.g = ld.g;
             d.steps = ld.steps;
             d.nsteps = ld.nsteps;
@@ -79,7 +81,7 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
     std::sort(large.begin(), large.end(), [](auto &x, auto &y) { return x.first > y.first; });
     for (auto &pr : large) {
         const BatchDesc &d = descs[pr.second];
-        const int tiles = (int)(d.g.S / C);
+        const int tiles = (int)(d.g.S / d.C);
         for (int opnd = 0; opnd < 2; ++opnd)
             for (int t = 0; t < tiles; ++t) items.push_back(WorkItem{IT_COLF, (int32_t)pr.second, t, opnd});
     }
@@ -90,7 +92,7 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
     }
     for (auto &pr : large) {
         const BatchDesc &d = descs[pr.second];
-        const int tiles = (int)(d.g.S / C);
+        const int tiles = (int)(d.g.S / d.C);
         for (int t = 0; t < tiles; ++t) items.push_back(WorkItem{IT_COLI, (int32_t)pr.second, t, 0});
     }
     *ws_bytes = ws;
@@ -98,14 +100,43 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
     return POLY_OK;
 }
 
-int batch_tile_width(int max_l) {
-    // Column tiles of the batch (8, 32 or 128 columns) hold T * C words in
-    // the persistent CTA's shared memory; wide tiles for short columns keep
-    // each item near 8K words, so per-item overhead stays small.
-    const int t = max_l - BATCH_SIGMA;
+// Built-in rule: column tiles of the batch hold T * C words in the
+// persistent CTA's shared memory; wide tiles for short columns keep each
+// item near 8K words, so per-item overhead stays small.
+int batch_width_default(int l) {
+    const int t = l - BATCH_SIGMA;
     if (t <= 6) return 128;
     if (t <= 8) return 32;
     return 8;
+}
+
+bool batch_width_valid(int l, int C) {
+    const int t = l - BATCH_SIGMA;
+    if (C != 8 && C != 32 && C != 128) return false;
+    if (t < 1 || t > LARGE_MAX_LOG_T) return false;
+    return ((size_t)C << t) * 4 <= BATCH_SMEM_MAX;
+}
+
+static std::mutex g_bw_mu;
+static std::map<int, int> g_bw;  // tuned widths, by log2 L
+
+int batch_width_for(int l) {
+    {
+        std::lock_guard<std::mutex> lk(g_bw_mu);
+        auto it = g_bw.find(l);
+        if (it != g_bw.end() && batch_width_valid(l, it->second)) return it->second;
+    }
+    return batch_width_default(l);
+}
+
+void set_batch_width(int l, int C) {
+    std::lock_guard<std::mutex> lk(g_bw_mu);
+    g_bw[l] = C;
+}
+
+std::map<int, int> all_batch_widths() {
+    std::lock_guard<std::mutex> lk(g_bw_mu);
+    return g_bw;
 }
 
 }  // namespace pm
@@ -116,7 +147,6 @@ struct polymul_batch {
     uint32_t p;
     int64_t count;
     PrimeCtx *ctx;
-    int C;
     size_t smem;
     std::vector<BatchDesc> h_descs;
     std::vector<WorkItem> h_items;
@@ -131,6 +161,7 @@ struct polymul_batch {
     int grid = 0;
     long long spin_limit = BATCH_SPIN_LIMIT;
     int withheld = 0;  // items dropped by polymul_batch_test_withhold
+    int64_t a_words = 0, b_words = 0;  // extent of the packed operands (validation)
 };
 
 static void batch_free(polymul_batch *b) {
@@ -175,9 +206,12 @@ int polymul_batch_create(uint32_t p, int64_t count, const int64_t *a_off, const 
     polymul_batch *b = new polymul_batch();
     b->p = p;
     b->count = count;
+    for (int64_t i = 0; i < count; ++i) {
+        b->a_words = std::max(b->a_words, a_off[i + 1]);
+        b->b_words = std::max(b->b_words, b_off[i + 1]);
+    }
     b->ctx = ctx;
-    b->C = batch_tile_width(max_l);
-    rc = build_worklist(ctx, count, za.data(), zb.data(), ao.data(), bo.data(), co.data(), b->C, b->h_descs,
+    rc = build_worklist(ctx, count, za.data(), zb.data(), ao.data(), bo.data(), co.data(), b->h_descs,
                         b->h_items, &b->ws_bytes, &b->smem);
     if (rc) {
         batch_free(b);
@@ -231,13 +265,15 @@ static BatchParams batch_params(polymul_batch *b, const uint32_t *a, const uint3
 static int batch_enqueue(polymul_batch *b, const uint32_t *a, const uint32_t *bb, uint32_t *c, cudaStream_t st) {
     BatchParams P = batch_params(b, a, bb, c);
     if (cudaMemsetAsync(b->ctrl, 0, (2 * b->count + 2) * sizeof(int), st) != cudaSuccess) return POLY_ECUDA;
-    return launch_batch(b->ctx->lazy, b->C, P, b->smem, &b->grid, st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
+    return launch_batch(b->ctx->lazy, P, b->smem, &b->grid, st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
 }
 
 int polymul_batch_exec_nograph(polymul_batch *b, const uint32_t *a, const uint32_t *bb, uint32_t *c, void *stream) {
     if (!b || !a || !bb || !c) return POLY_ENULL;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = batch_enqueue(b, a, bb, c, st);
+    int rc = validate_coeffs(b->p, a, b->a_words, bb, b->b_words, st);
+    if (rc) return rc;
+    rc = batch_enqueue(b, a, bb, c, st);
     if (rc) return rc;
     return cudaEventRecord(b->last, st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
 }
@@ -245,6 +281,10 @@ int polymul_batch_exec_nograph(polymul_batch *b, const uint32_t *a, const uint32
 int polymul_batch_exec(polymul_batch *b, const uint32_t *a, const uint32_t *bb, uint32_t *c, void *stream) {
     if (!b || !a || !bb || !c) return POLY_ENULL;
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        int rc = validate_coeffs(b->p, a, b->a_words, bb, b->b_words, st);
+        if (rc) return rc;
+    }
     auto key = std::make_tuple((uintptr_t)a, (uintptr_t)bb, (uintptr_t)c, (uintptr_t)0);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {

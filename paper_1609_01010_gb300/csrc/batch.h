@@ -1,6 +1,7 @@
 // batch.h -- work-list structures of the persistent batched kernel (shared by
 // the batch plan and the server).
 #pragma once
+#include <map>
 #include <vector>
 
 #include "host.h"
@@ -24,6 +25,7 @@ struct BatchDesc {
     int32_t nsteps;
     int32_t large;
     int32_t logT, k;  // small products
+    int32_t C;        // large products: column-tile width (8, 32 or 128 words)
 };
 
 struct BatchParams {
@@ -47,10 +49,18 @@ constexpr size_t BATCH_SMEM_MAX = 64 * 1024;
 // ~1.6 s of polling at 128 ns per poll before a wait is declared failed.
 constexpr long long BATCH_SPIN_LIMIT = 1ll << 24;
 
-cudaError_t launch_batch(bool lazy, int C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st);
+cudaError_t launch_batch(bool lazy, const BatchParams &P, size_t smem, int *grid, cudaStream_t st);
+// Work list of `count` products; each large product's column tiles have the
+// width batch_width_for(l) of its transform length 2^l.
 int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_t *zb, const uint64_t *a_off,
-                   const uint64_t *b_off, const uint64_t *c_off, int C, std::vector<BatchDesc> &descs,
+                   const uint64_t *b_off, const uint64_t *c_off, std::vector<BatchDesc> &descs,
                    std::vector<WorkItem> &items, uint64_t *ws_bytes, size_t *smem_bytes);
-int batch_tile_width(int max_l);
+// Column-tile width of a product of length 2^l inside a batch: the tuned
+// table (polymul_autotune, polymul_load_schedules) or the built-in rule.
+int batch_width_for(int l);
+int batch_width_default(int l);
+bool batch_width_valid(int l, int C);
+void set_batch_width(int l, int C);
+std::map<int, int> all_batch_widths();
 
 }  // namespace pm

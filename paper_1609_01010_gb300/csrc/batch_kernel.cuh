@@ -23,7 +23,21 @@ __device__ __forceinline__ bool wait_count(const int *ctr, int target, int *stat
     return true;
 }
 
-template <class A, int C>
+// Column items of a product run at its own tile width (8, 32 or 128 words).
+template <class A>
+__device__ __forceinline__ void colf_body_w(int C, const LargeDesc &d, int tile, int opnd, ModParams m, TwTables tw) {
+    if (C == 128) colf_body<A, 128>(d, tile, opnd, m, tw);
+    else if (C == 32) colf_body<A, 32>(d, tile, opnd, m, tw);
+    else colf_body<A, 8>(d, tile, opnd, m, tw);
+}
+template <class A>
+__device__ __forceinline__ void coli_body_w(int C, const LargeDesc &d, int tile, ModParams m, TwTables tw) {
+    if (C == 128) coli_body<A, 128>(d, tile, m, tw);
+    else if (C == 32) coli_body<A, 32>(d, tile, m, tw);
+    else coli_body<A, 8>(d, tile, m, tw);
+}
+
+template <class A>
 // Three resident CTAs per SM (at most 85 registers a thread; the largest
 // item's shared memory, 64 KB for a 16-row one-CTA product, allows three):
 // the items' barrier and load waits are latency-bound, and the extra CTA per
@@ -41,7 +55,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
         if (threadIdx.x == 0) {
             bool ok = true;
             if (w.kind == IT_ROW)
-                ok = wait_count(P.counters + 2 * w.prod, 2 * (int)(bd.g.S / C), P.status, P.spin_limit);
+                ok = wait_count(P.counters + 2 * w.prod, 2 * (int)(bd.g.S / bd.C), P.status, P.spin_limit);
             else if (w.kind == IT_COLI)
                 ok = wait_count(P.counters + 2 * w.prod + 1, (int)bd.g.k, P.status, P.spin_limit);
             s_ok = ok;
@@ -79,9 +93,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
                 d.steps = bd.steps;
                 d.nsteps = bd.nsteps;
                 d.prune = 1;
-                if (w.kind == IT_COLF) colf_body<A, C>(d, w.idx, w.opnd, P.m, P.tw);
+                if (w.kind == IT_COLF) colf_body_w<A>(bd.C, d, w.idx, w.opnd, P.m, P.tw);
                 else if (w.kind == IT_ROW) row_body_ool<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
-                else coli_body<A, C>(d, w.idx, P.m, P.tw);
+                else coli_body_w<A>(bd.C, d, w.idx, P.m, P.tw);
             }
         }
         __threadfence();  // each thread's outputs visible device-wide before the signal
@@ -91,7 +105,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
     }
 }
 
-template <class A, int C>
+template <class A>
 static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
     static std::mutex mu;
     static std::map<int, int> occ;  // device -> blocks per SM
@@ -103,9 +117,9 @@ static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_o
         std::lock_guard<std::mutex> lk(mu);
         auto it = occ.find(dev);
         if (it == occ.end()) {
-            e = cudaFuncSetAttribute(k_batch<A, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM_MAX);
+            e = cudaFuncSetAttribute(k_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM_MAX);
             if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A, C>, BATCH_THREADS, BATCH_SMEM_MAX);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A>, BATCH_THREADS, BATCH_SMEM_MAX);
             if (e != cudaSuccess) return e;
             if (per_sm < 1) per_sm = 1;
             occ[dev] = per_sm;
@@ -119,7 +133,7 @@ static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_o
     if (grid > P.nitems) grid = P.nitems;
     if (grid < 1) grid = 1;
     *grid_out = grid;
-    k_batch<A, C><<<grid, BATCH_THREADS, smem, st>>>(P);
+    k_batch<A><<<grid, BATCH_THREADS, smem, st>>>(P);
     return cudaGetLastError();
 }
 

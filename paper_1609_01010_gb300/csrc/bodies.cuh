@@ -39,7 +39,7 @@ __device__ __forceinline__ void small_body(const SmallDesc &d, ModParams m, TwTa
     u32 *sa = smem, *sb = smem + T * S;
     const u32 p = m.p;
     const int zba = (int)((d.za + S - 1) / S), zbb = (int)((d.zb + S - 1) / S);
-    ColFwdArgs X{sa, d.a, nullptr, d.za, 0u, SMALL_LOG_S, T, LOGT, zba, d.k, d.prune != 0, tw.fwd, p};
+    ColFwdArgs X{sa, d.a, nullptr, d.za, 0u, SMALL_LOG_S, T, LOGT, zba, d.k, d.prune != 0, tw.fwd, p, tw.status};
     colf_tile<A, S, LAY_SWZ>(X, false);
     X.sm = sb;
     X.g = d.b;
@@ -59,9 +59,12 @@ __device__ __forceinline__ void small_body(const SmallDesc &d, ModParams m, TwTa
         srow_inv<A, SMALL_LOG_S, NP - 1>(xa, sa + w * S, lane, LOGT, (u32)w, tw.inv, p);
     }
     __syncthreads();
-    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p, tw.fwd, nullptr};
+    const ColInvArgs Y{sa, nullptr, d.c, d.n, 0u, SMALL_LOG_S, d.k, tw.inv, p, tw.fwd, nullptr, tw.status};
     coli_steps<A, S, LAY_SWZ>(Y, d.steps, d.nsteps);
-    for (int64_t e = threadIdx.x; e < d.n; e += blockDim.x) d.c[e] = A::to_canon(sa[swz((u32)e)], p);
+    for (int64_t e = threadIdx.x; e < d.n; e += blockDim.x) {
+        PM_DCHECK(sa[swz((u32)e)] < A::bound(p) && e < ((int64_t)T << SMALL_LOG_S), tw.status);
+        d.c[e] = A::to_canon(sa[swz((u32)e)], p);
+    }
     __syncthreads();
 }
 
@@ -128,7 +131,7 @@ __device__ __forceinline__ void colf_compute(const LargeDesc &d, int tile, int o
     int zb = z > c0 ? (int)((z - c0 + S - 1) / S) : 0;
     if (zb > T) zb = T;
     const ColFwdArgs X{buf, nullptr, opnd ? d.wb : d.wa, z, (u32)c0, d.g.sigma, T, t, zb,
-                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p};
+                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p, tw.status};
     if (t == 0) {
         for (int c = threadIdx.x; c < C; c += blockDim.x) X.W[c0 + c] = buf[col_elem_addr<C, LAY_TILE>(0, c)];
         __syncthreads();
@@ -155,7 +158,7 @@ __device__ __forceinline__ void colf_compute_ct(const LargeDesc &d, int tile, in
     int zb = z > c0 ? (int)((z - c0 + S - 1) / S) : 0;
     if (zb > T) zb = T;
     const ColFwdArgs X{buf, nullptr, opnd ? d.wb : d.wa, z, (u32)c0, d.g.sigma, T, TL, zb,
-                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p};
+                       d.prune ? (int)d.g.k : T, d.prune != 0, tw.fwd, m.p, tw.status};
     colf_tile_ct<A, C, TL>(X);
 }
 
@@ -196,15 +199,20 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
     stage_tw<SIGMA>(twb, tw.fwd, t, ib);
     if constexpr (EARLY) stage_tw<UL>(twlo, tw.inv, t, ib);
     cp_async_commit();
+    // The pointwise constant, fetched now so its latency is behind the passes.
+    const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
     pdl_wait();  // the rows come from the column-stage kernel
     u32 xa[16], xb[16];
     srow2_load_g<SIGMA>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
     cp_async_wait<0>();
     __syncthreads();
     srow2_fwd_1b<A, SIGMA, 0, EARLY>(xa, xb, buf, twb, tid, p, tw.inv, t, ib);
-    const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) xa[i] = A::pointwise(xa[i], xb[i], cs, m);
+    for (int i = 0; i < 16; ++i) {
+        PM_DCHECK(xa[i] < 2 * A::bound(p) && xb[i] < 2 * A::bound(p) && ib < (u32)d.g.k, tw.status);
+        xa[i] = A::pointwise(xa[i], xb[i], cs, m);
+        PM_DCHECK(xa[i] < A::bound(p), tw.status);
+    }
     RowTw rt;
     if constexpr (EARLY) {
         cp_async_wait_all();  // this thread's own last-pass inverse twiddles
@@ -258,7 +266,7 @@ template <class A, int C>
 __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw) {
     const u32 c0 = (u32)tile * C;
     const int T = (int)d.g.T, k = (int)d.g.k;
-    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p, tw.fwd, nullptr};
+    const ColInvArgs X{buf, d.wa, d.c, d.n, c0, d.g.sigma, k, tw.inv, m.p, tw.fwd, nullptr, tw.status};
     if (d.g.t == 0) {
         for (int c = threadIdx.x; c < C; c += blockDim.x)
             if ((int64_t)(c0 + c) < d.n) d.c[c0 + c] = A::to_canon(buf[col_elem_addr<C, LAY_TILE>(0, c)], m.p);
@@ -278,7 +286,8 @@ __device__ __forceinline__ void coli_compute(const LargeDesc &d, int tile, u32 *
 template <class A, int C, int TL>
 __device__ __forceinline__ void coli_compute_ct(const LargeDesc &d, int tile, u32 *buf, ModParams m, TwTables tw,
                                              const uint2 *top) {
-    const ColInvArgs X{buf, d.wa, d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p, tw.fwd, top};
+    const ColInvArgs X{buf,   d.wa,   d.c, d.n, (u32)tile * C, d.g.sigma, (int)d.g.k, tw.inv, m.p, tw.fwd, top,
+                       tw.status};
     coli_tile_ct<A, C, TL>(X);
 }
 

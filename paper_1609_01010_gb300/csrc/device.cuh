@@ -27,6 +27,21 @@
 
 namespace pm {
 
+// Debug builds (compiled with PM_DEBUG_CHECKS=1): range and index checks in
+// the kernels.  A failed check records POLY_EDEBUG_CHECK (-11) in the
+// device status word (polymul_device_status) and the kernel goes on; nothing
+// traps.  In ordinary builds the checks compile to nothing.
+#if defined(PM_DEBUG_CHECKS) && PM_DEBUG_CHECKS
+#define PM_DCHECK(cond, status)                                    \
+    do {                                                           \
+        if (!(cond) && (status)) atomicCAS((status), 0, -11);      \
+    } while (0)
+#else
+#define PM_DCHECK(cond, status) \
+    do {                        \
+    } while (0)
+#endif
+
 __device__ __forceinline__ u32 swz(u32 w) { return w ^ (((w >> 5) & 7u) << 2); }
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
@@ -700,6 +715,7 @@ struct ColFwdArgs {
     bool prune;
     const uint2 *tw;
     u32 p;
+    int *status = nullptr;  // device status word (debug-build checks)
 };
 
 // One forward pass of R levels starting at depth s0.
@@ -740,7 +756,11 @@ __device__ __forceinline__ void colf_pass(const ColFwdArgs &X, int s0) {
             const int sh = logJ + X.logS;
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q)
-                if ((int)(r0 + ((u32)q << logJ)) < X.k) X.W[e0 + ((u32)q << sh)] = x[q];
+                if ((int)(r0 + ((u32)q << logJ)) < X.k) {
+                    PM_DCHECK(x[q] < 2 * A::bound(X.p) && c < C && (int64_t)(X.c0 + c) < ((int64_t)1 << X.logS),
+                              X.status);
+                    X.W[e0 + ((u32)q << sh)] = x[q];
+                }
         } else {
             const ColAddr<C, LAY> ad(r0, c, logJ);
 #pragma unroll
@@ -802,6 +822,7 @@ struct ColInvArgs {
     // coli_tile_ct only: the top three levels' twiddles in shared memory,
     // top[e] = fwd[e] and top[8 + e] = inv[e] for tree nodes e = 1..7
     const uint2 *top;
+    int *status = nullptr;  // device status word (debug-build checks)
 };
 
 // Inverse pass of R levels [lev0, lev0+R) of the subtree rooted at (s_root,
@@ -835,6 +856,7 @@ __device__ __forceinline__ void coli_pass(const ColInvArgs &X, int lev0, int s_r
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q) {
                 const u32 e = e0 + ((u32)q << sh);
+                PM_DCHECK(x[q] < A::bound(X.p), X.status);
                 if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[q], X.p);
             }
         } else {
@@ -940,8 +962,12 @@ __device__ __forceinline__ void colf_pass_ct(const ColFwdArgs &X, u32 copymask) 
             const int sh = logJ + X.logS;
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q)
-                if ((int)(r0 + ((u32)q << logJ)) < X.k)
+                if ((int)(r0 + ((u32)q << logJ)) < X.k) {
+                    PM_DCHECK(x[q] < 2 * A::bound(X.p) && y[q] < 2 * A::bound(X.p) &&
+                                  (int64_t)(X.c0 + c + 1) < ((int64_t)1 << X.logS),
+                              X.status);
                     *reinterpret_cast<uint2 *>(X.W + e0 + ((u32)q << sh)) = make_uint2(x[q], y[q]);
+                }
         } else {
             ct_store2<C, logJ, R>(x, y, X.sm, rc, H0);
         }
@@ -1233,6 +1259,7 @@ __device__ __forceinline__ void coli_tile_ct(const ColInvArgs &X) {
         for (int b = 0; b < NQ; ++b) {
             if (b >= q) break;
             const u32 e = e0 + ((u32)b << (LOGB + X.logS));
+            PM_DCHECK(x[b] < A::bound(X.p) && y[b] < A::bound(X.p) && c + 1 < C, X.status);
             if ((int64_t)e < X.n) X.out[e] = A::to_canon(x[b], X.p);
             if ((int64_t)e + 1 < X.n) X.out[e + 1] = A::to_canon(y[b], X.p);
         }

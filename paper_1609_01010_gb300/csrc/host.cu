@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -131,6 +132,54 @@ int *device_status_ptr() {
     }
     ptrs[dev] = (int *)p;
     return (int *)p;
+}
+
+// ------------------------------------------------------------ validation
+// With validation on, the entry points check that their inputs are residues
+// (below p) with one pass over them before any product work, and return
+// POLY_EINVAL_COEF otherwise.  The check synchronises the caller's stream.
+static std::atomic<int> g_validate{0};
+static __device__ int g_pm_badcoef;
+
+__global__ void k_check_range(const u32 *__restrict__ x, int64_t n, u32 p, int *bad) {
+    bool any = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        any |= x[i] >= p;
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicExch(bad, 1);
+}
+
+bool validation_on() { return g_validate.load(std::memory_order_relaxed) != 0; }
+
+int validate_coeffs(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t zb, cudaStream_t st) {
+    if (!validation_on()) return POLY_OK;
+    static std::mutex mu;  // one flag per device, one check at a time
+    static std::map<int, int *> flags;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLY_ECUDA;
+    auto it = flags.find(dev);
+    if (it == flags.end()) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_pm_badcoef);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(validation flag)");
+        it = flags.emplace(dev, (int *)ptr).first;
+    }
+    int *flag = it->second;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    const int threads = 256;
+    for (int o = 0; o < 2 && e == cudaSuccess; ++o) {
+        const u32 *x = o ? b : a;
+        const int64_t n = o ? zb : za;
+        if (!x || n <= 0) continue;
+        const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 1216);
+        k_check_range<<<blocks, threads, 0, st>>>(x, n, p, flag);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "coefficient validation");
+    return h ? POLY_EINVAL_COEF : POLY_OK;
 }
 
 // ------------------------------------------------------------ prime registry
@@ -369,26 +418,29 @@ int get_steps(PrimeCtx *ctx, int64_t T, int64_t k, const ItftStep **d_steps, int
 // ------------------------------------------------------------ schedules
 static std::mutex g_sched_mu;
 static std::map<int, Schedule> g_sched;  // autotuned, by log2 L
+static std::atomic<uint64_t> g_sched_version{1};  // bumped by every schedule change
 
 // Defaults from timing every valid (sigma, C) on GB300 with back-to-back
-// products (polymul_autotune measures the same way); the row kernel and the
-// column ITFT start early under programmatic dependent launch, so the best
-// split differs from one that isolated launches would pick.
+// products mod 469762049 (polymul_autotune measures the same way); the row
+// kernel and the column ITFT start early under programmatic dependent
+// launch, so the best split differs from one that isolated launches would
+// pick.  C = 32 selects the TMA-fed column kernels.
 Schedule default_schedule(int l) {
     switch (l) {
-        case 14: return Schedule{11, 128};
-        case 15: return Schedule{9, 8};
-        case 16:
-        case 17: return Schedule{10, 32};
-        case 18: return Schedule{11, 32};
-        case 19: return Schedule{12, 32};
-        case 20: return Schedule{11, 8};
-        case 21:
-        case 22: return Schedule{12, 8};
-        case 10: return Schedule{9, 8};
-        case 11: return Schedule{9, 128};
-        case 12: return Schedule{9, 32};
+        case 10:
+        case 11:
+        case 12: return Schedule{9, 128};
         case 13: return Schedule{11, 128};
+        case 14:
+        case 15: return Schedule{9, 8};
+        case 16: return Schedule{11, 128};
+        case 17: return Schedule{10, 32};
+        case 18: return Schedule{9, 8};
+        case 19: return Schedule{10, 8};
+        case 20: return Schedule{11, 8};
+        case 21: return Schedule{12, 8};
+        case 22: return Schedule{12, 32};
+        case 23: return Schedule{13, 32};
         default: return l < 10 ? Schedule{9, 8} : Schedule{13, 8};
     }
 }
@@ -415,6 +467,7 @@ Schedule schedule_for(int l) {
 void set_schedule(int l, Schedule s) {
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched[l] = s;
+    g_sched_version.fetch_add(1);
 }
 
 std::map<int, Schedule> all_schedules() {
@@ -525,6 +578,50 @@ int64_t large_workspace_words(int64_t n, int l, Schedule sch, bool prune) {
     return 2 * g.k * g.S;
 }
 
+// Per-thread cache of recently prepared product shapes: a repeated shape
+// (the common case of a caller looping over same-size products) skips the
+// prime validation, the mutex-guarded context, step-list and schedule
+// lookups.  An entry stays valid because prime contexts and step lists live
+// until the process exits and twiddle tables only grow (retired ones stay
+// allocated); a schedule change (autotuning, a loaded table) bumps
+// g_sched_version and so misses every entry.
+
+struct PlanEntry {
+    uint64_t ver = 0;
+    int dev = -1, l = 0, small_max_l = 0;
+    u32 p = 0, root = 0;
+    int64_t n = 0;
+    bool prune = false;
+    PrimeCtx *ctx = nullptr;
+    Schedule sch{0, 0};
+    Geometry g{};
+    const ItftStep *steps = nullptr;
+    int nsteps = 0;
+    int logT = 0;
+    int64_t k = 0;
+};
+constexpr int PLAN_CACHE = 8;
+
+static PlanEntry *plan_lookup(int dev, u32 p, u32 root, int l, int64_t n, bool prune, int small_max_l) {
+    static thread_local PlanEntry cache[PLAN_CACHE];
+    const uint64_t ver = g_sched_version.load(std::memory_order_acquire);
+    const uint64_t h = ((uint64_t)p * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)n * 0xC2B2AE3D27D4EB4Full) ^
+                       ((uint64_t)l << 7) ^ ((uint64_t)prune << 5) ^ (uint64_t)dev ^ ((uint64_t)small_max_l << 11);
+    PlanEntry &e = cache[(h >> 29) % PLAN_CACHE];
+    if (e.ver == ver && e.dev == dev && e.p == p && e.root == root && e.l == l && e.n == n && e.prune == prune &&
+        e.small_max_l == small_max_l)
+        return &e;
+    e.ver = 0;  // filled by the caller after a miss
+    e.dev = dev;
+    e.p = p;
+    e.root = root;
+    e.l = l;
+    e.n = n;
+    e.prune = prune;
+    e.small_max_l = small_max_l;
+    return &e;
+}
+
 int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t zb, u32 *c, int l, bool prune,
                 cudaStream_t st, u32 *workspace, int64_t n_out, int small_max_l) {
     if (!a || !b || !c) return POLY_ENULL;
@@ -533,22 +630,75 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     // depend on L), so their tables must reach depth 9.
     const bool small = l <= std::min(small_max_l, SMALL_MAX_LOG_L);
     const int need = (small && l < SMALL_LOG_S) ? SMALL_LOG_S : l;
-    int rc = get_prime(p, root, need, &ctx, st);
-    if (rc) return rc;
+    const int64_t n = n_out < 0 ? za + zb - 1 : n_out;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLY_ECUDA;
+    PlanEntry *pe = plan_lookup(dev, p, root, l, n, prune, small_max_l);
+    const bool hit = pe->ver != 0;
+    int rc;
+    if (hit) {
+        ctx = pe->ctx;
+    } else {
+        rc = get_prime(p, root, need, &ctx, st);
+        if (rc) return rc;
+    }
     if (small) {
         SmallDesc d;
-        rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d, n_out);
-        if (rc) return rc;
+        if (hit) {
+            d.a = a;
+            d.b = b;
+            d.c = c;
+            d.za = za;
+            d.zb = zb;
+            d.n = n;
+            d.logT = pe->logT;
+            d.k = (int32_t)pe->k;
+            d.steps = pe->steps;
+            d.nsteps = pe->nsteps;
+            d.prune = prune ? 1 : 0;
+        } else {
+            rc = prepare_small(ctx, a, za, b, zb, c, l, prune, &d, n_out);
+            if (rc) return rc;
+            pe->ctx = ctx;
+            pe->logT = d.logT;
+            pe->k = d.k;
+            pe->steps = d.steps;
+            pe->nsteps = d.nsteps;
+            pe->ver = g_sched_version.load(std::memory_order_acquire);
+        }
         cudaEvent_t *ev = prof_events(0);
         if (ev) cudaEventRecord(ev[0], st);
         cudaError_t e = launch_small(ctx->lazy, d.logT, nullptr, &d, 1, ctx->m, ctx->tw, st);
         if (ev) cudaEventRecord(ev[1], st);
         return e == cudaSuccess ? POLY_OK : cuda_fail(e, "one-CTA product launch");
     }
-    const Schedule sch = schedule_for(l);
     LargeDesc d;
-    rc = prepare_large(ctx, a, za, b, zb, c, l, prune, sch, &d, n_out);
-    if (rc) return rc;
+    Schedule sch;
+    if (hit) {
+        sch = pe->sch;
+        d.a = a;
+        d.b = b;
+        d.c = c;
+        d.wa = d.wb = nullptr;
+        d.za = za;
+        d.zb = zb;
+        d.n = n;
+        d.g = pe->g;
+        d.steps = pe->steps;
+        d.nsteps = pe->nsteps;
+        d.prune = prune ? 1 : 0;
+    } else {
+        const uint64_t ver = g_sched_version.load(std::memory_order_acquire);
+        sch = schedule_for(l);
+        rc = prepare_large(ctx, a, za, b, zb, c, l, prune, sch, &d, n_out);
+        if (rc) return rc;
+        pe->ctx = ctx;
+        pe->sch = sch;
+        pe->g = d.g;
+        pe->steps = d.steps;
+        pe->nsteps = d.nsteps;
+        pe->ver = ver;
+    }
     const size_t bytes = (size_t)2 * d.g.k * d.g.S * sizeof(u32);
     u32 *ws = workspace;
     if (!ws) {
@@ -568,7 +718,7 @@ int run_product(u32 p, u32 root, const u32 *a, int64_t za, const u32 *b, int64_t
     return e == cudaSuccess ? POLY_OK : cuda_fail(e, "three-kernel product launch");
 }
 
-static void keep_pool_memory() {
+void keep_pool_memory() {
     static std::once_flag once;
     std::call_once(once, [] {
         int dev = 0;
@@ -666,6 +816,7 @@ const char *polymul_strerror(int s) {
         case POLY_EBUSY: return "request exceeds the server memory budget";
         case POLY_ENOTFOUND: return "unknown ticket";
         case POLY_EINVAL_COEF: return "an input coefficient is outside [0, p)";
+        case POLY_EDEBUG_CHECK: return "a range or index check of the debug build failed in a kernel";
         default: return "unknown status";
     }
 }
@@ -684,6 +835,11 @@ int polymul_device_status(int clear) {
         if (cudaMemcpy(p, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return POLY_ECUDA;
     }
     return v;
+}
+
+int polymul_set_validate(int on) {
+    g_validate.store(on ? 1 : 0);
+    return POLY_OK;
 }
 
 int polymul_profile_begin(void) {
@@ -735,6 +891,12 @@ int polymul_mod_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t 
     const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
     const int l = ceil_log2(n);
     if (l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
+    if (validation_on()) {
+        u32 root = 0;
+        int rc = validate_prime(p, &root);
+        if (!rc) rc = validate_coeffs(p, a, za, b, zb, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
     return run_product(p, 0, a, za, b, zb, c, l, true, (cudaStream_t)stream, nullptr);
 }
 
@@ -753,13 +915,72 @@ int polymul_mod_padded_async(uint32_t p, const uint32_t *a, int64_t da, const ui
     const int l = ceil_log2(Lp);
     if (l > POLY_MAX_LOG_L) return POLY_ETOO_LONG;
     keep_pool_memory();
+    if (validation_on()) {
+        u32 root = 0;
+        int rc = validate_prime(p, &root);
+        if (!rc) rc = validate_coeffs(p, a, za, b, zb, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
     return run_product(p, 0, a, za, b, zb, c, l, false, (cudaStream_t)stream, nullptr);
+}
+
+// Host-buffer products on `st`, asynchronous: small ones in place where the
+// device walks the host page tables, the others staged through a
+// stream-ordered device buffer.  Pinned host buffers move by the copy
+// engines (they leave every SM to the products that run meanwhile on other
+// streams); pageable ones by the all-SM copy kernels where the device can
+// address them, else by the runtime's staged copies.
+static int host_product_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                              cudaStream_t st) {
+    if (!a || !b || !c) return POLY_ENULL;
+    if (da < 0 || db < 0) return POLY_EINVAL;
+    keep_pool_memory();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLY_ECUDA;
+    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
+    const bool in_place = host_memory_in_place(dev);
+    if (in_place && n <= HOST_IN_PLACE_MAX_N) return polymul_mod_async(p, a, da, b, db, c, st);
+    auto pinned = [](const void *ptr) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeHost;
+    };
+    const bool pin_in = pinned(a) && pinned(b), pin_out = pinned(c);
+    // staging buffers at 16-byte boundaries (vector copies)
+    const int64_t za4 = (za + 3) & ~(int64_t)3, zb4 = (zb + 3) & ~(int64_t)3;
+    u32 *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, (size_t)(za4 + zb4 + n) * 4, st) != cudaSuccess) return POLY_ENOMEM;
+    u32 *da_ = buf, *db_ = buf + za4, *dc_ = buf + za4 + zb4;
+    int rc = POLY_OK;
+    if (in_place && !pin_in) {
+        if (launch_copy_words(a, da_, za, b, db_, zb, st) != cudaSuccess) rc = POLY_ECUDA;
+    } else if (cudaMemcpyAsync(da_, a, (size_t)za * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+               cudaMemcpyAsync(db_, b, (size_t)zb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = POLY_ECUDA;
+    }
+    if (!rc) rc = polymul_mod_async(p, da_, da, db_, db, dc_, st);
+    if (!rc) {
+        if (in_place && !pin_out) {
+            if (launch_copy_words(dc_, c, n, nullptr, nullptr, 0, st) != cudaSuccess) rc = POLY_ECUDA;
+        } else if (cudaMemcpyAsync(c, dc_, (size_t)n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            rc = POLY_ECUDA;
+        }
+    }
+    if (cudaFreeAsync(buf, st) != cudaSuccess && !rc) rc = POLY_ECUDA;
+    return rc;
+}
+
+int polymul_mod_host_async(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c,
+                           void *stream) {
+    return host_product_async(p, a, da, b, db, c, (cudaStream_t)stream);
 }
 
 int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *b, int64_t db, uint32_t *c) {
     if (!a || !b || !c) return POLY_ENULL;
     if (da < 0 || db < 0) return POLY_EINVAL;
-    keep_pool_memory();
     static thread_local cudaStream_t st = nullptr;
     static thread_local int st_dev = -1;
     int dev = 0;
@@ -768,36 +989,7 @@ int polymul_mod_host(uint32_t p, const uint32_t *a, int64_t da, const uint32_t *
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return POLY_ECUDA;
         st_dev = dev;
     }
-    const int64_t za = da + 1, zb = db + 1, n = za + zb - 1;
-    const bool in_place = host_memory_in_place(dev);
-    if (in_place && n <= HOST_IN_PLACE_MAX_N) {
-        // Small products: the kernels read a and b and write c in place.
-        int rc = polymul_mod_async(p, a, da, b, db, c, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
-        return rc;
-    }
-    // staging buffers at 16-byte boundaries (vector copies)
-    const int64_t za4 = (za + 3) & ~(int64_t)3, zb4 = (zb + 3) & ~(int64_t)3;
-    u32 *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, (size_t)(za4 + zb4 + n) * 4, st) != cudaSuccess) return POLY_ENOMEM;
-    u32 *da_ = buf, *db_ = buf + za4, *dc_ = buf + za4 + zb4;
-    int rc = POLY_OK;
-    if (in_place) {
-        // Every SM moves 16-byte vectors over the coherent link.
-        if (launch_copy_words(a, da_, za, b, db_, zb, st) != cudaSuccess) rc = POLY_ECUDA;
-    } else if (cudaMemcpyAsync(da_, a, (size_t)za * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-               cudaMemcpyAsync(db_, b, (size_t)zb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        rc = POLY_ECUDA;
-    }
-    if (!rc) rc = polymul_mod_async(p, da_, da, db_, db, dc_, st);
-    if (!rc) {
-        if (in_place) {
-            if (launch_copy_words(dc_, c, n, nullptr, nullptr, 0, st) != cudaSuccess) rc = POLY_ECUDA;
-        } else if (cudaMemcpyAsync(c, dc_, (size_t)n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-            rc = POLY_ECUDA;
-        }
-    }
-    cudaFreeAsync(buf, st);
+    int rc = host_product_async(p, a, da, b, db, c, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
     return rc;
 }

@@ -54,12 +54,22 @@ struct AuxStreams {
 };
 int aux_streams(AuxStreams **out);
 
+// The device's default stream-ordered pool keeps memory it has grown to
+// (release threshold = unlimited), so a transient allocation does not map
+// and unmap memory at every synchronisation.  Once per process.
+void keep_pool_memory();
+
 u32 h_powmod(u64 b, u64 e, u32 p);
 u32 h_invmod(u32 a, u32 p);
 uint2 shoup_pair(u32 w, u32 p);
 int ceil_log2(int64_t n);
 
 int validate_prime(u32 p, u32 *root);
+// Validation mode (polymul_set_validate): whether it is on, and the check of
+// a[0..za) and b[0..zb) against p on stream st (synchronous; POLY_OK when
+// validation is off).  Null operands are skipped.
+bool validation_on();
+int validate_coeffs(u32 p, const u32 *a, int64_t za, const u32 *b, int64_t zb, cudaStream_t st);
 int get_prime(u32 p, u32 root, int need_l, PrimeCtx **out, cudaStream_t st);
 // prescaled: the spectral rows arrive multiplied by 1/h for their FULL
 // record (the product paths fold that into the pointwise constant), so the

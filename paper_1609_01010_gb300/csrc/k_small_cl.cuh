@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     {
         const int S = G::S;
         const int zba = (int)((d.za + S - 1) / S), zbb = (int)((d.zb + S - 1) / S);
-        ColFwdArgs X{tile_a, d.a, nullptr, d.za, c0, SMALL_LOG_S, G::T, LOGT, zba, k, d.prune != 0, tw.fwd, p};
+        ColFwdArgs X{tile_a, d.a, nullptr, d.za, c0, SMALL_LOG_S, G::T, LOGT, zba, k, d.prune != 0, tw.fwd, p,
+                     tw.status};
         colf_tile<A, G::CP, LAY_SWZ>(X, false);
         X.sm = tile_b;
         X.g = d.b;
@@ -105,11 +106,12 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     cl.sync();
 
     // 4. ITFT column stage and store
-    const ColInvArgs Y{tile_a, nullptr, d.c, d.n, c0, SMALL_LOG_S, k, tw.inv, p, tw.fwd, nullptr};
+    const ColInvArgs Y{tile_a, nullptr, d.c, d.n, c0, SMALL_LOG_S, k, tw.inv, p, tw.fwd, nullptr, tw.status};
     coli_steps<A, G::CP, LAY_SWZ>(Y, d.steps, d.nsteps);
     for (int e = threadIdx.x; e < k * G::CP; e += blockDim.x) {
         const int r = e / G::CP, lc = e % G::CP;
         const int64_t o = (int64_t)r * G::S + c0 + lc;
+        PM_DCHECK(tile_a[swz((u32)(r * G::CP + lc))] < A::bound(p), tw.status);
         if (o < d.n) d.c[o] = A::to_canon(tile_a[swz((u32)(r * G::CP + lc))], p);
     }
 }

@@ -332,5 +332,11 @@ extern "C" int polymul_mod_radix_async(uint32_t p, const uint32_t *a, int64_t da
     if (!a || !b || !c) return POLY_ENULL;
     if (da < 0 || db < 0 || m < 1 || m > radix::MAXM || (m & 1) == 0) return POLY_EINVAL;
     if (m == 1) return polymul_mod_async(p, a, da, b, db, c, stream);
+    if (validation_on()) {
+        u32 root = 0;
+        int rc = validate_prime(p, &root);
+        if (!rc) rc = validate_coeffs(p, a, da + 1, b, db + 1, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
     return radix_product(p, a, da + 1, b, db + 1, c, m, (cudaStream_t)stream);
 }

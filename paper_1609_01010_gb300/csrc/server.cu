@@ -2,19 +2,25 @@
 //
 // submit() queues a request and returns a ticket.  A scheduler thread admits
 // queued requests in arrival order while the bytes they hold (operands,
-// output and workspace) fit the memory budget, and hands the admitted
-// requests of one prime, as a group, to a free stream.  POLY_SERVE_BATCH
-// runs the group's small and medium requests (L <= 2^17) as one launch of
-// the persistent batched kernel whose work list holds them all -- when there
-// are at least SRV_BATCH_MIN of them -- and the rest as plain products behind
-// it (at light load a short work list only adds its build and upload to the
-// latency); POLY_SERVE_PLAIN runs every
-// request as its own plain product (1 or 3 kernels) -- the
-// one-launch-per-product comparator.  Requests that arrive while launches
-// are running are admitted into the next group on another stream as soon as
-// budget and a stream are free, so their work overlaps on the GPU.  A host
-// callback enqueued after each group stamps its completion time; latency =
-// completion - submit.
+// output and workspace) fit the memory budget, and hands admitted requests
+// of one prime, as a group, to a free stream.  Requests that arrive while
+// launches are running are admitted into the next group on another stream
+// as soon as budget and a stream are free, so their work overlaps on the
+// GPU.  Each group ends with an event; the scheduler thread polls the
+// events of the groups in flight (it spins while there is work or recent
+// activity and sleeps on a condition variable only after 2 ms idle), so a
+// completion is seen within about a microsecond; latency = that moment -
+// submit.
+//
+// POLY_SERVE_BATCH (the serving form): one stream in four (at least one)
+// is a high-priority lane that takes only small requests (L <= 2^SRV_BATCH_MAX_L), the others
+// take every request, large ones first, so the CTAs of small products are
+// scheduled ahead of the pending CTAs of large ones instead of queueing
+// behind them; a group's small requests run as one launch of the persistent
+// batched kernel when there are at least SRV_BATCH_MIN of them (a lone one
+// runs plain), the rest as plain products behind it.  POLY_SERVE_PLAIN (the comparator)
+// runs every request as its own plain product (1 or 3 kernels) on streams of
+// equal priority, groups in arrival order.
 #include <stdint.h>
 #include <string.h>
 
@@ -45,10 +51,11 @@ constexpr size_t SRV_STAGE_BYTES = (size_t)32 << 20;
 // on their own: they run as plain products (the three-kernel path with its
 // tuned schedule) behind the group's batched launch.
 constexpr int SRV_BATCH_MAX_L = 17;
-// ... and a group batches its small requests only when it has at least this
-// many: below that (light load) the work-list build and upload cost more
-// latency than the plain products' launches.
-constexpr size_t SRV_BATCH_MIN = 8;
+// ... and a group batches its small requests when it has at least this
+// many: a burst of requests that queued while the lanes were busy then costs
+// the scheduler thread one work-list upload and one launch instead of one
+// to three launches per request (a lone request runs plain).
+constexpr size_t SRV_BATCH_MIN = 2;
 
 struct SrvReq {
     uint64_t ticket;
@@ -64,7 +71,9 @@ struct SrvLaunch;
 
 struct SrvStream {
     cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after each group launched on st
     bool busy = false;
+    bool small_only = false;  // POLY_SERVE_BATCH: a high-priority lane for small requests
     char *pinned = nullptr;
     size_t pinned_bytes = 0;
 };
@@ -78,8 +87,6 @@ struct SrvLaunch {
     void *dbuf = nullptr;
     int *status_dev = nullptr;
     int *status_host = nullptr;
-    double t_done = 0;
-    std::atomic<bool> finished{false};
 };
 
 }  // namespace pm
@@ -96,6 +103,7 @@ struct polymul_server {
     std::deque<SrvReq> pending;
     std::map<uint64_t, int> state;  // 0 queued, 1 running, 2 done
     std::map<uint64_t, int> result;
+    std::map<uint64_t, double> latency;  // microseconds, done tickets
     std::vector<SrvLaunch *> inflight;
     std::vector<double> lat_us;
     uint64_t in_use = 0;
@@ -103,10 +111,8 @@ struct polymul_server {
     bool stop = false;
     std::thread th;
     std::map<u32, PrimeCtx *> ctx;
-    // Wake-ups of the scheduler (new request, finished launch, stop).  The
-    // host callback of a launch takes only this mutex, never `mu`, and the
-    // scheduler never holds `mu` across a CUDA call: a CUDA call that
-    // synchronises the device can then never wait on a blocked callback.
+    // Wake-ups of a sleeping scheduler (new request, stop).  The scheduler
+    // never holds `mu` across a CUDA call.
     std::mutex wake_mu;
     std::condition_variable wake_cv;
     uint64_t wake_seq = 0;
@@ -120,13 +126,6 @@ static void srv_wake(polymul_server *s) {
         ++s->wake_seq;
     }
     s->wake_cv.notify_all();
-}
-
-static void CUDART_CB srv_done_cb(void *arg) {
-    SrvLaunch *L = (SrvLaunch *)arg;
-    L->t_done = now_us();
-    L->finished.store(true, std::memory_order_release);
-    srv_wake((polymul_server *)L->srv);
 }
 
 // Work-list bytes a request adds to a launch's staging area (upper bound).
@@ -184,12 +183,11 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
             co[i] = (uint64_t)(uintptr_t)batched[i].c;
             max_l = std::max(max_l, ceil_log2(batched[i].n));
         }
-        const int C = batch_tile_width(max_l);
         std::vector<BatchDesc> descs;
         std::vector<WorkItem> items;
         uint64_t ws_bytes = 0;
         size_t smem = 0;
-        int rc = build_worklist(ctx, cnt, za.data(), zb.data(), ao.data(), bo.data(), co.data(), C, descs, items,
+        int rc = build_worklist(ctx, cnt, za.data(), zb.data(), ao.data(), bo.data(), co.data(), descs, items,
                                 &ws_bytes, &smem);
         if (rc) {
             delete L;
@@ -233,7 +231,7 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
         // status word back to pinned host memory, behind the kernel on the stream
         L->status_host = (int *)(h + stage);
         if (cudaMemcpyAsync(dbuf, h, stage, cudaMemcpyHostToDevice, ss.st) != cudaSuccess ||
-            launch_batch(ctx->lazy, C, P, smem, &grid, ss.st) != cudaSuccess ||
+            launch_batch(ctx->lazy, P, smem, &grid, ss.st) != cudaSuccess ||
             cudaMemcpyAsync(L->status_host, P.status, sizeof(int), cudaMemcpyDeviceToHost, ss.st) != cudaSuccess) {
             cudaFreeAsync(dbuf, ss.st);
             delete L;
@@ -254,7 +252,7 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
         L->t_submit.push_back(r.t_submit);
         L->bytes += r.bytes;
     }
-    if (cudaLaunchHostFunc(ss.st, srv_done_cb, L) != cudaSuccess) {
+    if (cudaEventRecord(ss.done, ss.st) != cudaSuccess) {
         if (L->dbuf) cudaFreeAsync(L->dbuf, ss.st);
         delete L;
         return POLY_ECUDA;
@@ -264,8 +262,49 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
     return POLY_OK;
 }
 
+// Before the first request: every kernel a request can meet is made
+// resident on the device (one zero product per transform length and prime,
+// one batched launch of the tile width the server's groups use), so no
+// request waits for a module to load, and the stream-ordered pool is grown
+// once to a part of the budget, so admissions do not map memory.
+static int srv_warm_up(polymul_server *s) {
+    keep_pool_memory();
+    const int max_l = BATCH_SIGMA + LARGE_MAX_LOG_T;
+    const int64_t half = (int64_t)1 << (max_l - 1);
+    cudaStream_t st = s->streams[0].st;
+    u32 *buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)4 * half * sizeof(u32)) != cudaSuccess) return POLY_ENOMEM;
+    u32 *a = buf, *b = buf + half, *c = buf + 2 * half;
+    int rc = cudaMemsetAsync(buf, 0, (size_t)4 * half * sizeof(u32), st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
+    for (auto &kv : s->ctx) {
+        const u32 p = kv.first;
+        for (int l = 1; l <= max_l && !rc; ++l) {
+            const int64_t z = (int64_t)1 << (l - 1);  // n = 2z - 1 needs L = 2^l
+            rc = run_product(p, 0, a, z, b, z, c, l, true, st, nullptr, -1, SMALL_MAX_LOG_L);
+        }
+        if (!rc) {  // the batched kernel of the groups' tile width (all batched requests have L <= 2^17)
+            const int64_t z = (int64_t)1 << (SRV_BATCH_MAX_L - 2), off[2] = {0, z}, coff[2] = {0, 2 * z - 1};
+            rc = polymul_mod_batched(p, 1, a, off, b, off, c, coff, st);
+        }
+    }
+    // grow the pool to min(budget, 1 GiB) once
+    void *big = nullptr;
+    const size_t reserve = std::min<size_t>(s->budget, (size_t)1 << 30);
+    if (!rc && cudaMallocAsync(&big, reserve, st) == cudaSuccess) cudaFreeAsync(big, st);
+    cudaGetLastError();
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = POLY_ECUDA;
+    cudaFree(buf);
+    return rc;
+}
+
+// Whether request r may run on stream lane ss (POLY_SERVE_BATCH lanes).
+static bool lane_takes(const SrvStream &ss, const SrvReq &r) {
+    return !ss.small_only || ceil_log2(r.n) <= SRV_BATCH_MAX_L;
+}
+
 static void srv_loop(polymul_server *s) {
     cudaSetDevice(s->dev);
+    double last_activity = now_us();
     for (;;) {
         uint64_t seq0;
         {
@@ -276,17 +315,21 @@ static void srv_loop(polymul_server *s) {
         // 1. retire finished launches (the in-flight list belongs to this thread)
         for (size_t i = 0; i < s->inflight.size();) {
             SrvLaunch *L = s->inflight[i];
-            if (!L->finished.load(std::memory_order_acquire)) {
+            const cudaError_t q = cudaEventQuery(s->streams[L->stream].done);
+            if (q == cudaErrorNotReady) {
                 ++i;
                 continue;
             }
-            const int st = L->status_host ? *L->status_host : POLY_OK;
+            const double t_done = now_us();
+            int st = L->status_host ? *L->status_host : POLY_OK;
+            if (q != cudaSuccess) st = POLY_ECUDA;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 for (size_t j = 0; j < L->tickets.size(); ++j) {
                     s->state[L->tickets[j]] = 2;
                     s->result[L->tickets[j]] = st;
-                    s->lat_us.push_back(L->t_done - L->t_submit[j]);
+                    s->lat_us.push_back(t_done - L->t_submit[j]);
+                    s->latency[L->tickets[j]] = t_done - L->t_submit[j];
                 }
                 s->in_use -= L->bytes;
             }
@@ -297,55 +340,88 @@ static void srv_loop(polymul_server *s) {
             s->inflight.erase(s->inflight.begin() + i);
             progress = true;
         }
-        // 2. admit queued requests onto free streams and launch them
-        for (size_t si = 0; si < s->streams.size(); ++si) {
-            if (s->streams[si].busy) continue;
-            std::vector<SrvReq> take;
-            uint64_t bytes = 0;
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                if (s->pending.empty()) break;
-                const u32 p = s->pending.front().p;
-                size_t staged = 4096;
-                for (auto it = s->pending.begin(); it != s->pending.end() && take.size() < 8192;) {
-                    if (it->p != p) {
-                        ++it;
-                        continue;
-                    }
-                    if (s->in_use + bytes + it->bytes > s->budget) break;
-                    const size_t sb = request_stage_bytes(it->n) + 1024;
-                    if (staged + sb > s->streams[si].pinned_bytes) break;
-                    staged += sb;
-                    bytes += it->bytes;
-                    s->state[it->ticket] = 1;
-                    take.push_back(*it);
-                    it = s->pending.erase(it);
-                }
-                s->in_use += bytes;
-            }
-            if (take.empty()) break;
-            const int rc = srv_launch(s, (int)si, take);
-            if (rc) {
+        // 2. admit queued requests onto free streams and launch them: in
+        // POLY_SERVE_BATCH the small-request lanes first, and the other lanes
+        // take large requests before small ones
+        for (int pass = 0; pass < 2; ++pass) {
+            for (size_t si = 0; si < s->streams.size(); ++si) {
+                SrvStream &ss = s->streams[si];
+                if (ss.busy || (pass == 0) != ss.small_only) continue;
+                std::vector<SrvReq> take;
+                uint64_t bytes = 0;
                 {
                     std::lock_guard<std::mutex> lk(s->mu);
-                    s->in_use -= bytes;
-                    for (auto &r : take) {
-                        s->state[r.ticket] = 2;
-                        s->result[r.ticket] = rc;
+                    if (s->pending.empty()) break;
+                    // the group's prime: that of the first request this lane may take
+                    // (large ones first on a general lane in the serving mode)
+                    const SrvReq *first = nullptr;
+                    if (s->mode == POLY_SERVE_BATCH && !ss.small_only)
+                        for (auto &r : s->pending)
+                            if (ceil_log2(r.n) > SRV_BATCH_MAX_L) {
+                                first = &r;
+                                break;
+                            }
+                    if (!first)
+                        for (auto &r : s->pending)
+                            if (lane_takes(ss, r)) {
+                                first = &r;
+                                break;
+                            }
+                    if (!first) continue;
+                    const u32 p = first->p;
+                    const bool large_first = s->mode == POLY_SERVE_BATCH && !ss.small_only &&
+                                             ceil_log2(first->n) > SRV_BATCH_MAX_L;
+                    size_t staged = 4096;
+                    for (auto it = s->pending.begin(); it != s->pending.end() && take.size() < 8192;) {
+                        const bool large = ceil_log2(it->n) > SRV_BATCH_MAX_L;
+                        if (it->p != p || !lane_takes(ss, *it) || (large_first && !large)) {
+                            ++it;
+                            continue;
+                        }
+                        if (s->in_use + bytes + it->bytes > s->budget) break;
+                        const size_t sb = request_stage_bytes(it->n) + 1024;
+                        if (staged + sb > ss.pinned_bytes) break;
+                        staged += sb;
+                        bytes += it->bytes;
+                        s->state[it->ticket] = 1;
+                        take.push_back(*it);
+                        it = s->pending.erase(it);
                     }
+                    s->in_use += bytes;
                 }
-                s->cv.notify_all();
+                if (take.empty()) continue;
+                const int rc = srv_launch(s, (int)si, take);
+                if (rc) {
+                    {
+                        std::lock_guard<std::mutex> lk(s->mu);
+                        s->in_use -= bytes;
+                        for (auto &r : take) {
+                            s->state[r.ticket] = 2;
+                            s->result[r.ticket] = rc;
+                        }
+                    }
+                    s->cv.notify_all();
+                }
+                progress = true;
             }
-            progress = true;
         }
+        bool idle;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+            idle = s->pending.empty() && s->inflight.empty();
         }
-        if (!progress) {
-            std::unique_lock<std::mutex> lk(s->wake_mu);
-            s->wake_cv.wait_for(lk, std::chrono::microseconds(500), [&] { return s->wake_seq != seq0; });
+        const double now = now_us();
+        if (progress || !idle) last_activity = now;
+        if (progress) continue;
+        if (!idle || now - last_activity < 2000.0) {
+            // work in flight, or recent activity: keep polling (completions
+            // and new requests are then seen within about a microsecond)
+            std::this_thread::yield();
+            continue;
         }
+        std::unique_lock<std::mutex> lk(s->wake_mu);
+        s->wake_cv.wait_for(lk, std::chrono::microseconds(500), [&] { return s->wake_seq != seq0; });
     }
 }
 
@@ -391,8 +467,18 @@ int polymul_server_create(size_t mem_budget_bytes, int n_streams, int mode, poly
         }
     }
     s->streams.resize(n_streams);
-    for (auto &ss : s->streams) {
-        if (cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking) != cudaSuccess) {
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+        delete s;
+        return POLY_ECUDA;
+    }
+    for (size_t si = 0; si < s->streams.size(); ++si) {
+        SrvStream &ss = s->streams[si];
+        // serving form: one lane in four (at least one) is a high-priority small-request lane
+        ss.small_only = mode == POLY_SERVE_BATCH && n_streams >= 2 && (int)si < std::max(1, n_streams / 4);
+        if (cudaStreamCreateWithPriority(&ss.st, cudaStreamNonBlocking, ss.small_only ? prio_greatest : prio_least) !=
+                cudaSuccess ||
+            cudaEventCreateWithFlags(&ss.done, cudaEventDisableTiming) != cudaSuccess) {
             delete s;
             return POLY_ECUDA;
         }
@@ -402,6 +488,16 @@ int polymul_server_create(size_t mem_budget_bytes, int n_streams, int mode, poly
             delete s;
             return POLY_ENOMEM;
         }
+    }
+    int rc = srv_warm_up(s);
+    if (rc) {
+        for (auto &ss : s->streams) {
+            if (ss.st) cudaStreamDestroy(ss.st);
+            if (ss.done) cudaEventDestroy(ss.done);
+            if (ss.pinned) cudaFreeHost(ss.pinned);
+        }
+        delete s;
+        return rc;
     }
     s->th = std::thread(srv_loop, s);
     *out = s;
@@ -417,6 +513,10 @@ int polymul_server_submit(polymul_server *s, uint32_t p, const uint32_t *a, int6
     if (ceil_log2(n) > BATCH_SIGMA + LARGE_MAX_LOG_T) return POLY_ETOO_LONG;
     const uint64_t bytes = request_bytes(za, zb);
     if (bytes > s->budget) return POLY_EBUSY;
+    if (validation_on()) {  // synchronous check on the legacy default stream before the request is queued
+        int rc = validate_coeffs(p, a, za, b, zb, nullptr);
+        if (rc) return rc;
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return POLY_EINVAL;
@@ -446,6 +546,17 @@ int polymul_server_wait(polymul_server *s, uint64_t ticket, int64_t timeout_ms) 
     const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return s->state[ticket] == 2; });
     if (!ok) return POLY_ETIMEOUT;
     return s->result[ticket];
+}
+
+int polymul_server_latency(polymul_server *s, uint64_t ticket, double *us) {
+    if (!s || !us) return POLY_ENULL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->state.find(ticket);
+    if (it == s->state.end()) return POLY_ENOTFOUND;
+    auto lt = s->latency.find(ticket);
+    if (lt == s->latency.end()) return POLY_EINVAL;  // not done yet (or failed before a launch)
+    *us = lt->second;
+    return POLY_OK;
 }
 
 int polymul_server_stats(polymul_server *s, double *out6) {
@@ -486,6 +597,7 @@ int polymul_server_destroy(polymul_server *s) {
             cudaStreamSynchronize(ss.st);
             cudaStreamDestroy(ss.st);
         }
+        if (ss.done) cudaEventDestroy(ss.done);
         if (ss.pinned) cudaFreeHost(ss.pinned);
     }
     delete s;

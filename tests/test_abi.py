@@ -71,5 +71,7 @@ def test_host_side_argument_checks(lib):
     assert L.polymul_probe_int(6, 1000, ctypes.byref(d1), ctypes.byref(d2)) == POLY_EINVAL  # unknown kind
     assert L.polymul_probe_int(0, 0, ctypes.byref(d1), ctypes.byref(d2)) == POLY_EINVAL  # no iterations
     assert L.polymul_probe_int(0, 1000, None, ctypes.byref(d2)) == POLY_ENULL
+    assert L.polymul_set_validate(0) == 0
+    assert L.polymul_strerror(-10).decode().startswith("an input coefficient")
     assert L.polymul_strerror(-6).decode().startswith("a bounded wait")
     assert b"sm_103a" in L.polymul_version()

@@ -209,3 +209,33 @@ def test_autotune_writes_and_loads_schedules(gpu, orc, tmp_path):
     B.polymul_mod(p, to_dev(a, gpu), len(a) - 1, to_dev(b, gpu), len(b) - 1, dc)
     assert np.array_equal(from_dev(dc), orc.polymul_tft(p, a, b))
     assert os.path.getsize(path) > 0
+
+
+def test_batch_tile_widths_from_the_table(gpu, orc, tmp_path):
+    """Every valid column-tile width per size class, loaded from a schedule
+    table ("batch_C"), gives the oracle's products; the table is restored."""
+    import json
+    import torch
+    from paper_1609_01010_gb300 import binding as B
+    saved = {l: B.polymul_get_batch_width(l) for l in range(14, 18)}
+    sched = {l: B.polymul_get_schedule(l) for l in range(14, 18)}
+    p, a, a_off, b, b_off, c_off = W.workload4(count=48, seed=W.SEED_BASE + 44)
+    da, db = to_dev(a, gpu), to_dev(b, gpu)
+    want = orc.polymul_tft_batch(p, a, a_off, b, b_off, c_off)
+    path = tmp_path / "widths.json"
+
+    def load(widths):
+        rows = [{"l": l, "sigma": sched[l][0], "C": sched[l][1], "us": 0.0, "batch_C": widths[l]}
+                for l in range(14, 18)]
+        path.write_text(json.dumps({"device": "test", "p": p, "schedules": rows}))
+        B.polymul_load_schedules(str(path))
+    try:
+        for C in (8, 32, 128):
+            load({l: C for l in range(14, 18)})
+            assert all(B.polymul_get_batch_width(l) == C for l in range(14, 18))
+            dc = torch.full((int(c_off[-1]),), -1, dtype=torch.int32, device=gpu)
+            B.polymul_mod_batched(p, da, a_off, db, b_off, dc, c_off)
+            torch.cuda.synchronize()
+            assert np.array_equal(from_dev(dc), want), C
+    finally:
+        load(saved)

@@ -85,3 +85,14 @@ def test_extreme_values_and_argument_checks(gpu, orc):
         B.polymul_cyclic_async(p, x, 9, x, 9, c, 8)  # za > N
     with pytest.raises(B.PolymulError):
         B.polymul_negacyclic_async(p, x, 0, x, 4, c, 8)  # empty operand
+
+
+@pytest.mark.parametrize("N,za,zb", [(1 << 17, 5000, 1 << 17), (1 << 21, 1 << 21, 1234567)])
+def test_negacyclic_twisted_second_prime(gpu, orc, N, za, zb):
+    """Power-of-two N (the twisted length-N path) mod 2013265921, unequal and
+    ragged operand lengths, against the folded oracle product."""
+    p = W.P2
+    a = W.coeffs(W.SEED_BASE + 72, za, p)
+    b = W.coeffs(W.SEED_BASE + 73, zb, p)
+    want = fold(orc.polymul_tft(p, a, b), N, p, -1)
+    assert np.array_equal(run("negacyclic", p, a, b, N, gpu), want)

@@ -272,3 +272,33 @@ def test_host_buffer_entry_point(gpu, orc):
         c2 = np.zeros(n + 3, dtype=np.uint32)
         B.polymul_mod_host(p, a2.ctypes.data + 4, len(a) - 1, b2.ctypes.data + 4, len(b) - 1, c2.ctypes.data + 12)
         assert np.array_equal(c2[3:], want) and not c2[:3].any()
+
+
+def test_host_async_on_several_streams(gpu, orc):
+    """polymul_mod_host_async: products on pinned and pageable host buffers
+    enqueued on three streams without waiting (in-place and staged sizes);
+    after the streams are synchronised every product equals the oracle."""
+    import torch
+    from paper_1609_01010_gb300 import binding as B
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    jobs = []
+    rng = np.random.default_rng(41)
+    for i, (z1, z2) in enumerate([(1000, 3000), (300000, 400000), (1 << 19, 1 << 19), (5, 7), (600000, 99999),
+                                  (1 << 20, 1 << 20)]):
+        p = P1 if i % 2 else P2
+        a = rnd(rng, z1, p)
+        b = rnd(rng, z2, p)
+        if i % 3 == 0:  # pageable numpy buffers
+            c = np.zeros(z1 + z2 - 1, dtype=np.uint32)
+            ha, hb, hc = a, b, c
+        else:  # pinned
+            ha = torch.from_numpy(a.view(np.int32)).pin_memory()
+            hb = torch.from_numpy(b.view(np.int32)).pin_memory()
+            hc = torch.zeros(z1 + z2 - 1, dtype=torch.int32).pin_memory()
+        B.polymul_mod_host_async(p, ha, z1 - 1, hb, z2 - 1, hc, streams[i % 3])
+        jobs.append((p, a, b, ha, hb, hc))
+    for s_ in streams:
+        s_.synchronize()
+    for p, a, b, ha, hb, hc in jobs:
+        got = hc if isinstance(hc, np.ndarray) else hc.numpy().view(np.uint32)
+        assert np.array_equal(got, orc.polymul_tft(p, a, b)), (p, len(a), len(b))
