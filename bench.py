@@ -69,7 +69,7 @@ REF_BUDGET_S = 120.0
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, default cache
 # control, so L2 starts cold) on the sources whose digest is recorded here;
 # any later change to those sources makes the figure stale and it reads null.
-ROW_TRAFFIC = {"bytes": 50368000 + 8192, "sources_sha256_16": "e6e698fe18844d47"}
+ROW_TRAFFIC = {"bytes": 50368768 + 55552000, "sources_sha256_16": "718b31c0b235fc70"}
 ROW_SOURCES = ("device.cuh", "bodies.cuh", "k_large.cuh", "modarith.cuh", "internal.h")
 
 
@@ -772,6 +772,16 @@ def serving(dev, B, seconds, rate=20000.0, budget=8 << 30, burst=20000):
             want = oracle.polymul_tft(q, pool_host[q][offa:offa + za], pool_host[q][offb:offb + zb])
             ok = ok and bool(np.array_equal(host_u32(pc), want))
             nchk += 1
+    # three times the configured rate for a few seconds (between the light
+    # configured load and saturation)
+    t3, prime3, da3, db3 = W.request_stream(rate=3 * rate, seconds=min(5.0, seconds), seed=W.SEED_BASE + 15)
+    load3 = {}
+    for name, mode in (("batch", B.SERVE_BATCH), ("plain", B.SERVE_PLAIN)):
+        stats, t_sub, t_all, _ = serve_run(dev, B, mode, t3, prime3, da3, db3, pools, budget, check_every=10 ** 9)
+        load3[name] = {"p50_us": stats["p50_us"], "p99_us": stats["p99_us"], "max_us": stats["max_us"],
+                       "throughput_req_per_s": len(t3) / t_all, "classes": stats["classes"]}
+    out["load_3x"] = dict(rate_req_per_s=3 * rate, seconds=min(5.0, seconds), requests=len(t3), **load3)
+    out["load_3x"]["p99_vs_plain"] = load3["plain"]["p99_us"] / load3["batch"]["p99_us"]
     # saturation: the first `burst` requests of the stream submitted back to back
     m = min(burst, len(t_arr))
     zeros = np.zeros(m)
