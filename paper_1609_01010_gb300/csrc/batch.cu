@@ -100,6 +100,16 @@ int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_
     return POLY_OK;
 }
 
+int uniform_width(const std::vector<BatchDesc> &descs) {
+    int c = 0;
+    for (const BatchDesc &d : descs) {
+        if (!d.large) continue;
+        if (c && d.C != c) return 0;
+        c = d.C;
+    }
+    return c ? c : 128;
+}
+
 // Built-in rule: column tiles of the batch hold T * C words in the
 // persistent CTA's shared memory; wide tiles for short columns keep each
 // item near 8K words, so per-item overhead stays small.
@@ -162,6 +172,7 @@ struct polymul_batch {
     long long spin_limit = BATCH_SPIN_LIMIT;
     int withheld = 0;  // items dropped by polymul_batch_test_withhold
     int64_t a_words = 0, b_words = 0;  // extent of the packed operands (validation)
+    int uniform_C = 0;                 // see uniform_width
 };
 
 static void batch_free(polymul_batch *b) {
@@ -217,6 +228,7 @@ int polymul_batch_create(uint32_t p, int64_t count, const int64_t *a_off, const 
         batch_free(b);
         return rc;
     }
+    b->uniform_C = uniform_width(b->h_descs);
     if (b->smem > BATCH_SMEM_MAX) {
         batch_free(b);
         return POLY_ETOO_LONG;
@@ -265,7 +277,7 @@ static BatchParams batch_params(polymul_batch *b, const uint32_t *a, const uint3
 static int batch_enqueue(polymul_batch *b, const uint32_t *a, const uint32_t *bb, uint32_t *c, cudaStream_t st) {
     BatchParams P = batch_params(b, a, bb, c);
     if (cudaMemsetAsync(b->ctrl, 0, (2 * b->count + 2) * sizeof(int), st) != cudaSuccess) return POLY_ECUDA;
-    return launch_batch(b->ctx->lazy, P, b->smem, &b->grid, st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
+    return launch_batch(b->ctx->lazy, b->uniform_C, P, b->smem, &b->grid, st) == cudaSuccess ? POLY_OK : POLY_ECUDA;
 }
 
 int polymul_batch_exec_nograph(polymul_batch *b, const uint32_t *a, const uint32_t *bb, uint32_t *c, void *stream) {

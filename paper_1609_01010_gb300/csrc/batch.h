@@ -49,7 +49,12 @@ constexpr size_t BATCH_SMEM_MAX = 64 * 1024;
 // ~1.6 s of polling at 128 ns per poll before a wait is declared failed.
 constexpr long long BATCH_SPIN_LIMIT = 1ll << 24;
 
-cudaError_t launch_batch(bool lazy, const BatchParams &P, size_t smem, int *grid, cudaStream_t st);
+// uniform_C: the common column-tile width of the launch's large products, or
+// 0 when they differ (the kernel then dispatches per product).
+cudaError_t launch_batch(bool lazy, int uniform_C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st);
+// The common column-tile width of the large products in descs (128 when
+// there is none), or 0 when they differ.
+int uniform_width(const std::vector<BatchDesc> &descs);
 // Work list of `count` products; each large product's column tiles have the
 // width batch_width_for(l) of its transform length 2^l.
 int build_worklist(PrimeCtx *ctx, int64_t count, const int64_t *za, const int64_t *zb, const uint64_t *a_off,

@@ -24,20 +24,30 @@ __device__ __forceinline__ bool wait_count(const int *ctr, int target, int *stat
 }
 
 // Column items of a product run at its own tile width (8, 32 or 128 words).
-template <class A>
+// CW != 0: every product of the launch has width CW (no dispatch); CW = 0:
+// the width is read per product.
+template <class A, int CW>
 __device__ __forceinline__ void colf_body_w(int C, const LargeDesc &d, int tile, int opnd, ModParams m, TwTables tw) {
-    if (C == 128) colf_body<A, 128>(d, tile, opnd, m, tw);
-    else if (C == 32) colf_body<A, 32>(d, tile, opnd, m, tw);
-    else colf_body<A, 8>(d, tile, opnd, m, tw);
+    if constexpr (CW != 0) {
+        colf_body<A, CW>(d, tile, opnd, m, tw);
+    } else {
+        if (C == 128) colf_body<A, 128>(d, tile, opnd, m, tw);
+        else if (C == 32) colf_body<A, 32>(d, tile, opnd, m, tw);
+        else colf_body<A, 8>(d, tile, opnd, m, tw);
+    }
 }
-template <class A>
+template <class A, int CW>
 __device__ __forceinline__ void coli_body_w(int C, const LargeDesc &d, int tile, ModParams m, TwTables tw) {
-    if (C == 128) coli_body<A, 128>(d, tile, m, tw);
-    else if (C == 32) coli_body<A, 32>(d, tile, m, tw);
-    else coli_body<A, 8>(d, tile, m, tw);
+    if constexpr (CW != 0) {
+        coli_body<A, CW>(d, tile, m, tw);
+    } else {
+        if (C == 128) coli_body<A, 128>(d, tile, m, tw);
+        else if (C == 32) coli_body<A, 32>(d, tile, m, tw);
+        else coli_body<A, 8>(d, tile, m, tw);
+    }
 }
 
-template <class A>
+template <class A, int CW>
 // Three resident CTAs per SM (at most 85 registers a thread; the largest
 // item's shared memory, 64 KB for a 16-row one-CTA product, allows three):
 // the items' barrier and load waits are latency-bound, and the extra CTA per
@@ -93,9 +103,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
                 d.steps = bd.steps;
                 d.nsteps = bd.nsteps;
                 d.prune = 1;
-                if (w.kind == IT_COLF) colf_body_w<A>(bd.C, d, w.idx, w.opnd, P.m, P.tw);
+                if (w.kind == IT_COLF) colf_body_w<A, CW>(bd.C, d, w.idx, w.opnd, P.m, P.tw);
                 else if (w.kind == IT_ROW) row_body_ool<A, BATCH_SIGMA>(d, (u32)w.idx, P.m, P.tw);
-                else coli_body_w<A>(bd.C, d, w.idx, P.m, P.tw);
+                else coli_body_w<A, CW>(bd.C, d, w.idx, P.m, P.tw);
             }
         }
         __threadfence();  // each thread's outputs visible device-wide before the signal
@@ -105,8 +115,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchParams P) {
     }
 }
 
-template <class A>
-static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
+template <class A, int CW>
+static cudaError_t launch_batch_cw(const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
     static std::mutex mu;
     static std::map<int, int> occ;  // device -> blocks per SM
     int dev = 0;
@@ -117,9 +127,11 @@ static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_o
         std::lock_guard<std::mutex> lk(mu);
         auto it = occ.find(dev);
         if (it == occ.end()) {
-            e = cudaFuncSetAttribute(k_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM_MAX);
+            e = cudaFuncSetAttribute(k_batch<A, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)BATCH_SMEM_MAX);
             if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A>, BATCH_THREADS, BATCH_SMEM_MAX);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A, CW>, BATCH_THREADS,
+                                                              BATCH_SMEM_MAX);
             if (e != cudaSuccess) return e;
             if (per_sm < 1) per_sm = 1;
             occ[dev] = per_sm;
@@ -133,8 +145,21 @@ static cudaError_t launch_batch_t(const BatchParams &P, size_t smem, int *grid_o
     if (grid > P.nitems) grid = P.nitems;
     if (grid < 1) grid = 1;
     *grid_out = grid;
-    k_batch<A><<<grid, BATCH_THREADS, smem, st>>>(P);
+    k_batch<A, CW><<<grid, BATCH_THREADS, smem, st>>>(P);
     return cudaGetLastError();
+}
+
+// uniform_C: the one column-tile width of every large product of the launch
+// (8, 32, 128; any of them when there is no large product), or 0 when the
+// widths differ.
+template <class A>
+static cudaError_t launch_batch_t(int uniform_C, const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
+    switch (uniform_C) {
+        case 8: return launch_batch_cw<A, 8>(P, smem, grid_out, st);
+        case 32: return launch_batch_cw<A, 32>(P, smem, grid_out, st);
+        case 128: return launch_batch_cw<A, 128>(P, smem, grid_out, st);
+        default: return launch_batch_cw<A, 0>(P, smem, grid_out, st);
+    }
 }
 
 }  // namespace pm

@@ -4,8 +4,8 @@
 
 namespace pm {
 
-cudaError_t launch_batch_lazy(const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
-    return launch_batch_t<Arith<true>>(P, smem, grid, st);
+cudaError_t launch_batch_lazy(int uniform_C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
+    return launch_batch_t<Arith<true>>(uniform_C, P, smem, grid, st);
 }
 
 }  // namespace pm

@@ -4,8 +4,8 @@
 
 namespace pm {
 
-cudaError_t launch_batch_strict(const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
-    return launch_batch_t<Arith<false>>(P, smem, grid, st);
+cudaError_t launch_batch_strict(int uniform_C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
+    return launch_batch_t<Arith<false>>(uniform_C, P, smem, grid, st);
 }
 
 }  // namespace pm

@@ -116,8 +116,9 @@ __device__ __forceinline__ uint2 lds_tw(const uint2 *p) {
 }
 
 // Two columns at once (x, y), sharing the twiddle loads; tw is the shared
-// memory copy of the table (lds_tw).
-template <class A, int R>
+// memory copy of the table (lds_tw).  ROOT: node0 is 0 (a group of the root's
+// pass), so each level's first node has twiddle 1 and needs no multiply.
+template <class A, int R, bool ROOT = false>
 __device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *tw, int lev0, u32 node0, u32 p,
                                             u32 copymask) {
 #pragma unroll
@@ -135,6 +136,14 @@ __device__ __forceinline__ void grp_fwd_cp2(u32 *x, u32 *y, const uint2 *tw, int
         } else {
 #pragma unroll
             for (int e = 0; e < (1 << d); ++e) {
+                if (ROOT && e == 0) {
+#pragma unroll
+                    for (int jj = 0; jj < half; ++jj) {
+                        A::ct_one(x[jj], x[jj + half], p);
+                        A::ct_one(y[jj], y[jj + half], p);
+                    }
+                    continue;
+                }
                 const uint2 w = lds_tw(tw + tw_index(lev0 + d, (node0 << d) + e));
 #pragma unroll
                 for (int jj = 0; jj < half; ++jj) {
@@ -956,7 +965,7 @@ __device__ __forceinline__ void colf_pass_ct(const ColFwdArgs &X, u32 copymask) 
         const u32 rc = r0 * C + c, H0 = tile_h<C>(r0) * C;
         u32 x[1 << R], y[1 << R];
         ct_load2<C, logJ, R>(x, y, X.sm, rc, H0);
-        grp_fwd_cp2<A, R>(x, y, X.tw, S0, v, X.p, copymask >> S0);
+        grp_fwd_cp2<A, R, S0 == 0>(x, y, X.tw, S0, v, X.p, copymask >> S0);  // S0 = 0: v is 0
         if constexpr (DST == IO_GLOBAL) {
             const u32 e0 = (r0 << X.logS) + X.c0 + c;
             const int sh = logJ + X.logS;
@@ -1111,11 +1120,19 @@ __device__ __forceinline__ void top_full_inv(u32 *x, u32 *y, const uint2 *top, u
         constexpr int h = M / 2;
         top_full_inv<A, h, S + 1, 2 * I>(x, y, top, p);
         top_full_inv<A, h, S + 1, 2 * I + 1>(x + h, y + h, top, p);
-        const uint2 w = top[8 + (1 << S) + I];
+        if constexpr (I == 0) {  // the first node of its level: twiddle 1
 #pragma unroll
-        for (int j = 0; j < h; ++j) {
-            A::gs(x[j], x[j + h], w, p);
-            A::gs(y[j], y[j + h], w, p);
+            for (int j = 0; j < h; ++j) {
+                A::gs_one(x[j], x[j + h], p);
+                A::gs_one(y[j], y[j + h], p);
+            }
+        } else {
+            const uint2 w = top[8 + (1 << S) + I];
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                A::gs(x[j], x[j + h], w, p);
+                A::gs(y[j], y[j + h], w, p);
+            }
         }
     }
 }

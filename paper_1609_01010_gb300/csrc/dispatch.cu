@@ -74,8 +74,8 @@ PM_DECL_TCOL(launch_tcoli_strict)
 
 cudaError_t launch_row_lazy(const LargeDesc &, ModParams, TwTables, cudaStream_t);
 cudaError_t launch_row_strict(const LargeDesc &, ModParams, TwTables, cudaStream_t);
-cudaError_t launch_batch_lazy(const BatchParams &, size_t, int *, cudaStream_t);
-cudaError_t launch_batch_strict(const BatchParams &, size_t, int *, cudaStream_t);
+cudaError_t launch_batch_lazy(int, const BatchParams &, size_t, int *, cudaStream_t);
+cudaError_t launch_batch_strict(int, const BatchParams &, size_t, int *, cudaStream_t);
 
 cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int items, int *grid) {
     static std::mutex mu;
@@ -212,8 +212,8 @@ cudaError_t launch_large(bool lazy, const LargeDesc &d, Schedule sch, ModParams 
     return e;
 }
 
-cudaError_t launch_batch(bool lazy, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
-    return lazy ? launch_batch_lazy(P, smem, grid, st) : launch_batch_strict(P, smem, grid, st);
+cudaError_t launch_batch(bool lazy, int uniform_C, const BatchParams &P, size_t smem, int *grid, cudaStream_t st) {
+    return lazy ? launch_batch_lazy(uniform_C, P, smem, grid, st) : launch_batch_strict(uniform_C, P, smem, grid, st);
 }
 
 }  // namespace pm

@@ -64,6 +64,26 @@ struct Arith {
         b = x - t + B;
     }
 
+    // ct with twiddle 1 (the first node of every tree level): no multiply,
+    // the upper input is only brought below B.  Same ranges as ct.
+    __device__ __forceinline__ static void ct_one(u32& a, u32& b, u32 p) {
+        const u32 B = bound(p);
+        const u32 x = umin32(a, a - B);
+        const u32 t = umin32(b, b - B);
+        a = x + t;
+        b = x - t + B;
+    }
+
+    // gs with twiddle 1: (x, y) -> (x + y, x - y).  Same ranges as gs.
+    __device__ __forceinline__ static void gs_one(u32& a, u32& b, u32 p) {
+        const u32 B = bound(p);
+        u32 s = a + b;
+        s = umin32(s, s - B);
+        const u32 d = a - b + B;
+        a = s;
+        b = umin32(d, d - B);
+    }
+
     // Gentleman-Sande inverse butterfly with the inverse twiddle w = r^-1:
     // (x, y) -> (x + y, (x - y) w).  Inputs and outputs in [0, B).
     __device__ __forceinline__ static void gs(u32& a, u32& b, uint2 w, u32 p) {

@@ -231,7 +231,7 @@ static int srv_launch(polymul_server *s, int si, std::vector<SrvReq> &reqs) {
         // status word back to pinned host memory, behind the kernel on the stream
         L->status_host = (int *)(h + stage);
         if (cudaMemcpyAsync(dbuf, h, stage, cudaMemcpyHostToDevice, ss.st) != cudaSuccess ||
-            launch_batch(ctx->lazy, P, smem, &grid, ss.st) != cudaSuccess ||
+            launch_batch(ctx->lazy, uniform_width(descs), P, smem, &grid, ss.st) != cudaSuccess ||
             cudaMemcpyAsync(L->status_host, P.status, sizeof(int), cudaMemcpyDeviceToHost, ss.st) != cudaSuccess) {
             cudaFreeAsync(dbuf, ss.st);
             delete L;
