@@ -370,9 +370,9 @@ int polymul_load_schedules(const char *json_path);
 int polymul_get_schedule(int l, int *sigma, int *C);
 
 /*
- * Column-tile width (8, 32 or 128 words) of a product of length L = 2^l
- * inside a batch (l in 14..22): tuned or built-in.  POLY_EINVAL outside that
- * range.
+ * Column-tile width (8, 32, 128, 256, 512, 1024 or 2048 words) of a product of length
+ * L = 2^l inside a batch (l in 14..22): tuned or built-in (the widest tile
+ * of T x C words that fits 64 KB).  POLY_EINVAL outside that range.
  */
 int polymul_get_batch_width(int l, int *C);
 

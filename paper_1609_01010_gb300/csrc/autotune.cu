@@ -150,7 +150,7 @@ int polymul_autotune(uint32_t p, int lo_log, int hi_log, const char *json_path) 
         cudaMemsetAsync(bb, 0x01, (size_t)count * 2 * z * 4, st);
         const int prev = batch_width_for(l);
         BRow best{l, 0, 1e30f};
-        for (int C : {8, 32, 128}) {
+        for (int C : {8, 32, 128, 256, 512, 1024, 2048}) {
             if (!batch_width_valid(l, C)) continue;
             set_batch_width(l, C);
             const float us = time_batch(p, l, count, bb, bb + count * z, bb + 2 * count * z, st, e0, e1);

@@ -110,19 +110,22 @@ int uniform_width(const std::vector<BatchDesc> &descs) {
     return c ? c : 128;
 }
 
-// Built-in rule: column tiles of the batch hold T * C words in the
-// persistent CTA's shared memory; wide tiles for short columns keep each
-// item near 8K words, so per-item overhead stays small.
+// Built-in rule: the widest column tile (of 8, 32, 128, 256, 512, 1024 or
+// 2048 columns)
+// whose T * C words fit the batched kernel's 64 KB of shared memory.  A
+// column item's fixed cost (fetching it, its dependency check, its fence and
+// barriers) is then spread over as many words as the shared memory allows:
+// a product of L = 2^14 (4 rows of 4096) has 2 + 4 + 1 items instead of
+// 64 + 4 + 32 with 128-column tiles.
 int batch_width_default(int l) {
-    const int t = l - BATCH_SIGMA;
-    if (t <= 6) return 128;
-    if (t <= 8) return 32;
+    for (int C : {2048, 1024, 512, 256, 128, 32, 8})
+        if (batch_width_valid(l, C)) return C;
     return 8;
 }
 
 bool batch_width_valid(int l, int C) {
     const int t = l - BATCH_SIGMA;
-    if (C != 8 && C != 32 && C != 128) return false;
+    if (C != 8 && C != 32 && C != 128 && C != 256 && C != 512 && C != 1024 && C != 2048) return false;
     if (t < 1 || t > LARGE_MAX_LOG_T) return false;
     return ((size_t)C << t) * 4 <= BATCH_SMEM_MAX;
 }

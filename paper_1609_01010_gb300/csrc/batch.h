@@ -25,7 +25,7 @@ struct BatchDesc {
     int32_t nsteps;
     int32_t large;
     int32_t logT, k;  // small products
-    int32_t C;        // large products: column-tile width (8, 32 or 128 words)
+    int32_t C;        // large products: column-tile width (8, 32, 128, 256, 512, 1024 or 2048 words)
 };
 
 struct BatchParams {

@@ -23,7 +23,7 @@ __device__ __forceinline__ bool wait_count(const int *ctr, int target, int *stat
     return true;
 }
 
-// Column items of a product run at its own tile width (8, 32 or 128 words).
+// Column items of a product run at its own tile width (8 .. 2048 words).
 // CW != 0: every product of the launch has width CW (no dispatch); CW = 0:
 // the width is read per product.
 template <class A, int CW>
@@ -31,7 +31,11 @@ __device__ __forceinline__ void colf_body_w(int C, const LargeDesc &d, int tile,
     if constexpr (CW != 0) {
         colf_body<A, CW>(d, tile, opnd, m, tw);
     } else {
-        if (C == 128) colf_body<A, 128>(d, tile, opnd, m, tw);
+        if (C == 2048) colf_body<A, 2048>(d, tile, opnd, m, tw);
+        else if (C == 1024) colf_body<A, 1024>(d, tile, opnd, m, tw);
+        else if (C == 512) colf_body<A, 512>(d, tile, opnd, m, tw);
+        else if (C == 256) colf_body<A, 256>(d, tile, opnd, m, tw);
+        else if (C == 128) colf_body<A, 128>(d, tile, opnd, m, tw);
         else if (C == 32) colf_body<A, 32>(d, tile, opnd, m, tw);
         else colf_body<A, 8>(d, tile, opnd, m, tw);
     }
@@ -41,7 +45,11 @@ __device__ __forceinline__ void coli_body_w(int C, const LargeDesc &d, int tile,
     if constexpr (CW != 0) {
         coli_body<A, CW>(d, tile, m, tw);
     } else {
-        if (C == 128) coli_body<A, 128>(d, tile, m, tw);
+        if (C == 2048) coli_body<A, 2048>(d, tile, m, tw);
+        else if (C == 1024) coli_body<A, 1024>(d, tile, m, tw);
+        else if (C == 512) coli_body<A, 512>(d, tile, m, tw);
+        else if (C == 256) coli_body<A, 256>(d, tile, m, tw);
+        else if (C == 128) coli_body<A, 128>(d, tile, m, tw);
         else if (C == 32) coli_body<A, 32>(d, tile, m, tw);
         else coli_body<A, 8>(d, tile, m, tw);
     }
@@ -150,8 +158,8 @@ static cudaError_t launch_batch_cw(const BatchParams &P, size_t smem, int *grid_
 }
 
 // uniform_C: the one column-tile width of every large product of the launch
-// (8, 32, 128; any of them when there is no large product), or 0 when the
-// widths differ.
+// (any width when there is no large product), or 0 when the widths differ;
+// widths 8, 32 and 128 have a kernel of their own, the others dispatch.
 template <class A>
 static cudaError_t launch_batch_t(int uniform_C, const BatchParams &P, size_t smem, int *grid_out, cudaStream_t st) {
     switch (uniform_C) {

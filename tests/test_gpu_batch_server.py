@@ -203,6 +203,7 @@ def test_autotune_writes_and_loads_schedules(gpu, orc, tmp_path):
     assert [r["l"] for r in table["schedules"]] == [14, 15, 16, 17]
     for r in table["schedules"]:
         assert 9 <= r["sigma"] <= 13 and r["C"] in (8, 32, 128) and r["us"] > 0
+        assert r["batch_C"] in (8, 32, 128, 256, 512, 1024, 2048) and r["batch_us"] > 0
     B.polymul_load_schedules(path)
     p, a, b = W.workload3(1 << 16)
     dc = torch.empty(2 * len(a) - 1, dtype=torch.int32, device=gpu)
@@ -212,8 +213,9 @@ def test_autotune_writes_and_loads_schedules(gpu, orc, tmp_path):
 
 
 def test_batch_tile_widths_from_the_table(gpu, orc, tmp_path):
-    """Every valid column-tile width per size class, loaded from a schedule
-    table ("batch_C"), gives the oracle's products; the table is restored."""
+    """Every valid column-tile width per size class (8 to 2048 columns, where
+    the tile fits 64 KB), loaded from a schedule table ("batch_C"), gives the
+    oracle's products; the table is restored."""
     import json
     import torch
     from paper_1609_01010_gb300 import binding as B
@@ -229,10 +231,13 @@ def test_batch_tile_widths_from_the_table(gpu, orc, tmp_path):
                 for l in range(14, 18)]
         path.write_text(json.dumps({"device": "test", "p": p, "schedules": rows}))
         B.polymul_load_schedules(str(path))
+    def fits(l, C):  # a tile of 2^(l-12) rows x C words within 64 KB
+        return (C << (l - 12)) * 4 <= 64 * 1024
     try:
-        for C in (8, 32, 128):
-            load({l: C for l in range(14, 18)})
-            assert all(B.polymul_get_batch_width(l) == C for l in range(14, 18))
+        for C in (8, 32, 128, 256, 512, 1024, 2048):
+            widths = {l: C if fits(l, C) else 8 for l in range(14, 18)}
+            load(widths)
+            assert all(B.polymul_get_batch_width(l) == widths[l] for l in range(14, 18))
             dc = torch.full((int(c_off[-1]),), -1, dtype=torch.int32, device=gpu)
             B.polymul_mod_batched(p, da, a_off, db, b_off, dc, c_off)
             torch.cuda.synchronize()
