@@ -199,14 +199,18 @@ __device__ __forceinline__ void grp_inv(u32 *x, const uint2 *__restrict__ itw, i
 }
 
 // ------------------------------------------------------ row-stage helpers
-template <int SIGMA, int P>
+// Pass P of a row of 2^SIGMA words held E words per thread (E = 16: one
+// warp per 512-word row, 4-level passes; E = 4 or 8: 2- or 3-level passes on
+// S/E threads of a CTA).
+template <int SIGMA, int P, int E = 16>
 struct RowPlan {
-    static constexpr int NP = (SIGMA + 3) / 4;  // passes
-    static constexpr int R = (P < NP - 1) ? 4 : (SIGMA - 4 * (NP - 1));
+    static constexpr int LE = ilog2c(E);             // levels of a full pass
+    static constexpr int NP = (SIGMA + LE - 1) / LE;  // passes
+    static constexpr int R = (P < NP - 1) ? LE : (SIGMA - LE * (NP - 1));
     static constexpr int S = 1 << SIGMA;
-    static constexpr int NT = S / 16;  // threads per row
-    static constexpr int NG = 16 >> R; // groups per thread
-    static constexpr int U0 = 4 * P;   // first sub-level of the pass
+    static constexpr int NT = S / E;   // threads per row
+    static constexpr int NG = E >> R;  // groups per thread
+    static constexpr int U0 = LE * P;  // first sub-level of the pass
 };
 
 // G + q*(S>>R) with S>>R a multiple of 256 never carries into bits [7:5],
@@ -279,9 +283,9 @@ __device__ __forceinline__ void ld_con_s(const u32 *buf, u32 G, u32 *x) {
 
 // Butterflies of one pass on the thread's groups.  Row ib sits at depth t;
 // its sub-node v at sub-level U0 is tree node (ib << U0) + v at depth t+U0.
-template <class A, int SIGMA, int P>
+template <class A, int SIGMA, int P, int E = 16>
 __device__ __forceinline__ void row_fwd_compute(u32 *x, u32 tid, int t, u32 ib, const uint2 *__restrict__ tw, u32 p) {
-    using RP = RowPlan<SIGMA, P>;
+    using RP = RowPlan<SIGMA, P, E>;
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 G = tid + g * RP::NT;
@@ -289,9 +293,9 @@ __device__ __forceinline__ void row_fwd_compute(u32 *x, u32 tid, int t, u32 ib, 
         grp_fwd<A, RP::R>(x + (g << RP::R), tw, t + RP::U0, (ib << RP::U0) + v, p);
     }
 }
-template <class A, int SIGMA, int P>
+template <class A, int SIGMA, int P, int E = 16>
 __device__ __forceinline__ void row_inv_compute(u32 *x, u32 tid, int t, u32 ib, const uint2 *__restrict__ itw, u32 p) {
-    using RP = RowPlan<SIGMA, P>;
+    using RP = RowPlan<SIGMA, P, E>;
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 G = tid + g * RP::NT;
@@ -627,6 +631,57 @@ __device__ __forceinline__ void srow_inv(u32 *x, u32 *buf, u32 tid, int t, u32 i
     for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(buf, tid + g * RP::NT, x + (g << RP::R));
     __syncwarp();
     if constexpr (P > 0) srow_inv<A, SIGMA, P - 1>(x, buf, tid, t, ib, itw, p);
+}
+
+// Rows spread over the threads of a CTA: NT = S/E threads per row, E words
+// each, passes of log2 E levels with block barriers between them (every
+// thread of the CTA reaches every barrier; `on` is false for the threads of
+// a row that is not needed, which skip the work).  Same Stockham layout as
+// srow_fwd / srow_inv (the row starts and ends in natural order in `buf`);
+// the twiddles come from the row's shared-memory copy (stage_tw layout).
+template <class A, int SIGMA, int E, int P>
+__device__ __forceinline__ void srowc_fwd(u32 *x, u32 *buf, u32 tid, bool on, const uint2 *twb, u32 p) {
+    using RP = RowPlan<SIGMA, P, E>;
+    if (on) {
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) ld_str_s<RP::R, RP::S>(buf, tid + g * RP::NT, x + (g << RP::R));
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) {
+            const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
+            grp_fwd_s<A, RP::R, RP::U0>(x + (g << RP::R), twb, v, p);
+        }
+    }
+    if constexpr (P < RP::NP - 1) {
+        __syncthreads();
+        if (on) {
+#pragma unroll
+            for (int g = 0; g < RP::NG; ++g) st_con_s<RP::R>(buf, tid + g * RP::NT, x + (g << RP::R));
+        }
+        __syncthreads();
+        srowc_fwd<A, SIGMA, E, P + 1>(x, buf, tid, on, twb, p);
+    }
+}
+template <class A, int SIGMA, int E, int P>
+__device__ __forceinline__ void srowc_inv(u32 *x, u32 *buf, u32 tid, bool on, const uint2 *itwb, u32 p) {
+    using RP = RowPlan<SIGMA, P, E>;
+    if (on) {
+        if constexpr (P < RP::NP - 1) {
+#pragma unroll
+            for (int g = 0; g < RP::NG; ++g) ld_con_s<RP::R>(buf, tid + g * RP::NT, x + (g << RP::R));
+        }
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) {
+            const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
+            grp_inv_s<A, RP::R, RP::U0>(x + (g << RP::R), itwb, v, p);
+        }
+    }
+    __syncthreads();
+    if (on) {
+#pragma unroll
+        for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(buf, tid + g * RP::NT, x + (g << RP::R));
+    }
+    __syncthreads();
+    if constexpr (P > 0) srowc_inv<A, SIGMA, E, P - 1>(x, buf, tid, on, itwb, p);
 }
 
 // ------------------------------------------------------ column-stage helpers
