@@ -66,10 +66,14 @@ REF_BUDGET_S = 120.0
 
 
 # DRAM bytes (read + write) of one k_row_fused launch at the headline size,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, default cache
-# control, so L2 starts cold) on the sources whose digest is recorded here;
-# any later change to those sources makes the figure stale and it reads null.
-ROW_TRAFFIC = {"bytes": 50368768 + 55552000, "sources_sha256_16": "718b31c0b235fc70"}
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, medians over 20
+# launches) on the sources whose digest is recorded here; any later change to
+# those sources makes the figures stale and they read null.  "bytes": with
+# --cache-control none, so L2 holds what the previous kernels left there, as
+# in the timed stream of products (the column stage's rows and the resident
+# twiddle tables are L2 hits); "bytes_cold_l2": with ncu's default cache
+# control, which flushes L2 before the launch (rows and twiddles from DRAM).
+ROW_TRAFFIC = {"bytes": 500096 + 994944, "bytes_cold_l2": 50369024 + 0, "sources_sha256_16": "e93abf19a8eaff68"}
 ROW_SOURCES = ("device.cuh", "bodies.cuh", "k_large.cuh", "modarith.cuh", "internal.h")
 
 
@@ -79,7 +83,8 @@ def row_kernel_traffic():
     for f in ROW_SOURCES:
         with open(os.path.join(ROOT, "paper_1609_01010_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return ROW_TRAFFIC["bytes"] if h.hexdigest()[:16] == ROW_TRAFFIC["sources_sha256_16"] else None
+    ok = h.hexdigest()[:16] == ROW_TRAFFIC["sources_sha256_16"]
+    return (ROW_TRAFFIC["bytes"], ROW_TRAFFIC["bytes_cold_l2"]) if ok else (None, None)
 
 
 def load_peaks():
@@ -877,7 +882,11 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_row_fused (row stage: forward x2, pointwise, inverse)",
                 "achieved": achieved, "peak": peak_tops, "unit": "Tintop/s",
                 "frac": (achieved / peak_tops) if achieved else None,
-                "traffic": row_kernel_traffic(),
+                "traffic": row_kernel_traffic()[0],
+                "traffic_cold_l2": row_kernel_traffic()[1],
+                "traffic_note": "ncu DRAM bytes per launch: traffic with L2 as the stream of products leaves it "
+                                "(--cache-control none), traffic_cold_l2 after ncu's L2 flush; the row data are "
+                                "16.8 MB read + 8.4 MB written per launch",
                 "peak_source": "measured on this GPU by polymul_probe_int kind 0 (the lazy forward butterfly of "
                                "the transform kernels, 16 independent register chains per thread, full occupancy): "
                                f"{int_peaks['forward butterfly']['per_s'] / 1e12:.3f} T butterflies/s x 7 ops",
