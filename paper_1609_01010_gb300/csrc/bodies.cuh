@@ -173,21 +173,23 @@ __device__ __noinline__ void colf_body(const LargeDesc d, int tile, int opnd, Mo
 }
 
 // Row ib: remaining sigma levels of both operands, pointwise product,
-// unscaled inverse; result overwrites wa's row.  blockDim must be S/16.
+// unscaled inverse; result overwrites wa's row.  blockDim must be S/E (E
+// words per thread: 16 in 4-level passes, or 8 / 4 in 3- / 2-level passes for
+// products with few rows, which then spread each row over more threads).
 // Shared memory (row_smem_bytes): one exchange buffer of S words, the row's
 // S-1 forward twiddles (8 bytes each) and, for sigma <= 12, the inverse
-// twiddles of the sub-levels before the last pass (2^8 entries).  Pass 0
+// twiddles of the sub-levels before the last pass (2^UL entries).  Pass 0
 // reads both rows from global memory while the twiddles arrive by cp.async;
 // the last pass's inverse twiddles are fetched during the forward passes
 // (srow2_fwd_1b, EARLY), so the inverse starts without a staging wait.  For
 // sigma = 13 (whose shared inverse levels would take 32 KB) the inverse
 // table is staged over the forward one after the pointwise product.
-template <class A, int SIGMA>
+template <class A, int SIGMA, int E = 16>
 __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m, TwTables tw) {
     u32 *smem = dyn_smem();
     constexpr int S = 1 << SIGMA;
-    constexpr int NP = RowPlan<SIGMA, 0>::NP;
-    constexpr int UL = row_last_u0<SIGMA>();
+    constexpr int NP = RowPlan<SIGMA, 0, E>::NP;
+    constexpr int UL = row_last_u0<SIGMA, E>();
     constexpr bool EARLY = SIGMA <= 12;
     u32 *buf = smem;
     uint2 *twb = reinterpret_cast<uint2 *>(smem + S);
@@ -202,13 +204,13 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
     // The pointwise constant, fetched now so its latency is behind the passes.
     const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
     pdl_wait();  // the rows come from the column-stage kernel
-    u32 xa[16], xb[16];
-    srow2_load_g<SIGMA>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
+    u32 xa[E], xb[E];
+    srow2_load_g<SIGMA, E>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
     cp_async_wait<0>();
     __syncthreads();
-    srow2_fwd_1b<A, SIGMA, 0, EARLY>(xa, xb, buf, twb, tid, p, tw.inv, t, ib);
+    srow2_fwd_1b<A, SIGMA, 0, EARLY, E>(xa, xb, buf, twb, tid, p, tw.inv, t, ib);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < E; ++i) {
         PM_DCHECK(xa[i] < 2 * A::bound(p) && xb[i] < 2 * A::bound(p) && ib < (u32)d.g.k, tw.status);
         xa[i] = A::pointwise(xa[i], xb[i], cs, m);
         PM_DCHECK(xa[i] < A::bound(p), tw.status);
@@ -224,7 +226,7 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
         __syncthreads();
         rt = RowTw{twb, twb, twb + (S >> 1)};
     }
-    srow2_inv<A, SIGMA, NP - 1>(xa, buf, rowa, rt, tid, p);
+    srow2_inv<A, SIGMA, NP - 1, E>(xa, buf, rowa, rt, tid, p);
     __syncthreads();
 }
 

@@ -420,36 +420,36 @@ __device__ __forceinline__ void grp_inv_s_lvl(u32 *x, const uint2 *twb, u32 v, u
 struct RowTw {
     const uint2 *lo, *mid, *top;
 };
-template <int SIGMA>
+template <int SIGMA, int E = 16>
 __host__ __device__ constexpr int row_last_u0() {
-    return 4 * (RowPlan<SIGMA, 0>::NP - 1);
+    return RowPlan<SIGMA, 0, E>::LE * (RowPlan<SIGMA, 0, E>::NP - 1);
 }
-template <int SIGMA, int LEV>
+template <int SIGMA, int LEV, int E = 16>
 __device__ __forceinline__ const uint2 *rt_level(const RowTw &t) {
     if constexpr (LEV == SIGMA - 1) return t.top;
-    else if constexpr (LEV >= row_last_u0<SIGMA>()) return t.mid + (1u << LEV);
+    else if constexpr (LEV >= row_last_u0<SIGMA, E>()) return t.mid + (1u << LEV);
     else return t.lo + (1u << LEV);
 }
-template <class A, int SIGMA, int R, int U0, int D>
+template <class A, int SIGMA, int R, int U0, int D, int E = 16>
 __device__ __forceinline__ void grp_inv_rt_lvl(u32 *x, const RowTw &rt, u32 v, u32 p) {
     if constexpr (D >= 0) {
         constexpr int half = 1 << (R - 1 - D);
         uint2 w[1 << D];
-        ld_tw_level<D>(w, rt_level<SIGMA, U0 + D>(rt), v);
+        ld_tw_level<D>(w, rt_level<SIGMA, U0 + D, E>(rt), v);
 #pragma unroll
         for (int e = 0; e < (1 << D); ++e)
 #pragma unroll
             for (int jj = 0; jj < half; ++jj) A::gs(x[e * 2 * half + jj], x[e * 2 * half + jj + half], w[e], p);
-        grp_inv_rt_lvl<A, SIGMA, R, U0, D - 1>(x, rt, v, p);
+        grp_inv_rt_lvl<A, SIGMA, R, U0, D - 1, E>(x, rt, v, p);
     }
 }
 
 // Copies of one thread's inverse twiddles for the last pass (groups
 // v = tid + g*NT): sub-level sigma-1 into top (entry 2^(sigma-1) + j at top[j]),
 // the pass's other levels (MID) into twb at their usual entries.
-template <int SIGMA, bool MID>
+template <int SIGMA, bool MID, int E = 16>
 __device__ __forceinline__ void row_last_inv_tw(uint2 *dst, const uint2 *__restrict__ itab, int t, u32 ib, u32 tid) {
-    using RP = RowPlan<SIGMA, RowPlan<SIGMA, 0>::NP - 1>;
+    using RP = RowPlan<SIGMA, RowPlan<SIGMA, 0, E>::NP - 1, E>;
     constexpr int U0 = RP::U0, R = RP::R;
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
@@ -516,10 +516,10 @@ __device__ __forceinline__ void srow2_fwd(u32 *xa, u32 *xb, u32 *ba, u32 *bb, co
 }
 
 // One operand's hand-over from forward pass P to pass P+1 through buf.
-template <int SIGMA, int P>
+template <int SIGMA, int P, int E = 16>
 __device__ __forceinline__ void row_xchg(u32 *x, u32 *buf, u32 tid) {
-    using RP = RowPlan<SIGMA, P>;
-    using RN = RowPlan<SIGMA, P + 1>;
+    using RP = RowPlan<SIGMA, P, E>;
+    using RN = RowPlan<SIGMA, P + 1, E>;
     __syncthreads();
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) st_con_s<RP::R>(buf, tid + g * RP::NT, x + (g << RP::R));
@@ -533,9 +533,9 @@ __device__ __forceinline__ void row_xchg(u32 *x, u32 *buf, u32 tid) {
 // passes operand a, then operand b, goes through `buf` (four barriers per
 // pass boundary instead of two, for half the shared memory).  The last pass
 // leaves the leaves in registers.
-template <int SIGMA>
+template <int SIGMA, int E = 16>
 __device__ __forceinline__ void srow2_load_g(u32 *xa, u32 *xb, const u32 *ga, const u32 *gb, u32 tid) {
-    using RP = RowPlan<SIGMA, 0>;
+    using RP = RowPlan<SIGMA, 0, E>;
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         ld_str_g<RP::R, RP::S>(ga, tid + g * RP::NT, xa + (g << RP::R));
@@ -550,13 +550,13 @@ __device__ __forceinline__ void srow2_load_g(u32 *xa, u32 *xb, const u32 *ga, co
 // the copy of its sub-level sigma-1 inverse twiddles into `buf` (exactly S
 // words), and right after the pass (its forward twiddles consumed) the copy
 // of its other inverse twiddles of that pass over the forward ones in twb.
-template <class A, int SIGMA, int P, bool EARLY>
+template <class A, int SIGMA, int P, bool EARLY, int E = 16>
 __device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, uint2 *twb, u32 tid, u32 p,
                                              const uint2 *__restrict__ itab, int t, u32 ib) {
-    using RP = RowPlan<SIGMA, P>;
+    using RP = RowPlan<SIGMA, P, E>;
     if constexpr (EARLY && P == RP::NP - 1) {
         __syncthreads();  // every thread has loaded its elements from buf
-        row_last_inv_tw<SIGMA, false>(reinterpret_cast<uint2 *>(buf), itab, t, ib, tid);
+        row_last_inv_tw<SIGMA, false, E>(reinterpret_cast<uint2 *>(buf), itab, t, ib, tid);
         cp_async_commit();
     }
 #pragma unroll
@@ -565,20 +565,20 @@ __device__ __forceinline__ void srow2_fwd_1b(u32 *xa, u32 *xb, u32 *buf, uint2 *
         grp_fwd_s2_lvl<A, RP::R, RP::U0, 0>(xa + (g << RP::R), xb + (g << RP::R), twb, v, p);
     }
     if constexpr (P < RP::NP - 1) {
-        row_xchg<SIGMA, P>(xa, buf, tid);
-        row_xchg<SIGMA, P>(xb, buf, tid);
-        srow2_fwd_1b<A, SIGMA, P + 1, EARLY>(xa, xb, buf, twb, tid, p, itab, t, ib);
+        row_xchg<SIGMA, P, E>(xa, buf, tid);
+        row_xchg<SIGMA, P, E>(xb, buf, tid);
+        srow2_fwd_1b<A, SIGMA, P + 1, EARLY, E>(xa, xb, buf, twb, tid, p, itab, t, ib);
     } else if constexpr (EARLY) {
-        row_last_inv_tw<SIGMA, true>(twb, itab, t, ib, tid);
+        row_last_inv_tw<SIGMA, true, E>(twb, itab, t, ib, tid);
         cp_async_commit();
     }
 }
 
 // Inverse passes from the leaves in registers; the last pass (P = 0) writes
 // the row to global memory in natural order.
-template <class A, int SIGMA, int P>
+template <class A, int SIGMA, int P, int E = 16>
 __device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const RowTw &rt, u32 tid, u32 p) {
-    using RP = RowPlan<SIGMA, P>;
+    using RP = RowPlan<SIGMA, P, E>;
     if constexpr (P < RP::NP - 1) {
 #pragma unroll
         for (int g = 0; g < RP::NG; ++g) ld_con_s<RP::R>(ba, tid + g * RP::NT, x + (g << RP::R));
@@ -586,7 +586,7 @@ __device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const RowT
 #pragma unroll
     for (int g = 0; g < RP::NG; ++g) {
         const u32 v = (tid + g * RP::NT) & ((1u << RP::U0) - 1u);
-        grp_inv_rt_lvl<A, SIGMA, RP::R, RP::U0, RP::R - 1>(x + (g << RP::R), rt, v, p);
+        grp_inv_rt_lvl<A, SIGMA, RP::R, RP::U0, RP::R - 1, E>(x + (g << RP::R), rt, v, p);
     }
     if constexpr (P == 0) {
 #pragma unroll
@@ -596,7 +596,7 @@ __device__ __forceinline__ void srow2_inv(u32 *x, u32 *ba, u32 *gdst, const RowT
 #pragma unroll
         for (int g = 0; g < RP::NG; ++g) st_str_s<RP::R, RP::S>(ba, tid + g * RP::NT, x + (g << RP::R));
         __syncthreads();
-        srow2_inv<A, SIGMA, P - 1>(x, ba, gdst, rt, tid, p);
+        srow2_inv<A, SIGMA, P - 1, E>(x, ba, gdst, rt, tid, p);
     }
 }
 

@@ -430,12 +430,12 @@ Schedule default_schedule(int l) {
         case 10:
         case 11:
         case 12: return Schedule{9, 128};
-        case 13: return Schedule{11, 128};
-        case 14:
-        case 15: return Schedule{9, 8};
-        case 16: return Schedule{11, 128};
-        case 17: return Schedule{10, 32};
-        case 18: return Schedule{9, 8};
+        case 13: return Schedule{10, 128};
+        case 14: return Schedule{9, 8};
+        case 15:
+        case 16: return Schedule{10, 8};
+        case 17:
+        case 18: return Schedule{11, 8};
         case 19: return Schedule{10, 8};
         case 20: return Schedule{11, 8};
         case 21: return Schedule{12, 8};

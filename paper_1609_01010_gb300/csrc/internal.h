@@ -80,12 +80,14 @@ constexpr int LARGE_MAX_LOG_T = 10;
 // of T / 2^RELAX_LOG_T (see make_geometry).
 constexpr int RELAX_LOG_T = 3;
 
-// Shared memory of one row of the row stage: one exchange buffer (S words),
-// the row's twiddles (S entries of 8 bytes, entry 0 unused) and, for
-// sigma <= 12, the 2^8 inverse twiddles of the sub-levels before its last
-// pass.
-inline size_t row_smem_bytes(int sigma) {
-    return ((size_t)1 << sigma) * 4 + ((size_t)1 << sigma) * 8 + (sigma <= 12 ? (size_t)256 * 8 : 0);
+// Shared memory of one row of the row stage held E words per thread: one
+// exchange buffer (S words), the row's twiddles (S entries of 8 bytes, entry
+// 0 unused) and, for sigma <= 12, the 2^UL inverse twiddles of the sub-levels
+// before its last pass (UL = log2(E) times the passes before the last).
+inline size_t row_smem_bytes(int sigma, int E = 16) {
+    const int le = E >= 16 ? 4 : (E >= 8 ? 3 : 2);
+    const int ul = le * ((sigma + le - 1) / le - 1);
+    return ((size_t)1 << sigma) * 4 + ((size_t)1 << sigma) * 8 + (sigma <= 12 ? ((size_t)8 << ul) : 0);
 }
 
 struct Schedule {

@@ -68,17 +68,31 @@ __global__ void __launch_bounds__(COL_THREADS, 6) k_col_fwd(const LargeDesc d, M
     }
 }
 
-// Resident CTAs per SM the row kernel is compiled for: what its shared
-// memory (S words of exchange buffer + S twiddles of 8 bytes) allows, so
-// registers never limit it further.
-constexpr int row_min_blocks(int sigma) {
-    return sigma >= 13 ? 2 : (sigma == 12 ? 4 : (sigma == 11 ? 8 : 16));
+// Resident CTAs per SM the row kernel is compiled for.  E = 16: what its
+// shared memory (S words of exchange buffer + S twiddles of 8 bytes) allows,
+// so registers never limit it further; E = 4 or 8 (S/E threads per row):
+// 64 registers a thread, at most 16 CTAs.
+constexpr int row_min_blocks(int sigma, int E = 16) {
+    return E == 16 ? (sigma >= 13 ? 2 : (sigma == 12 ? 4 : (sigma == 11 ? 8 : 16)))
+                   : (65536 / (64 * ((1 << sigma) / E)) < 16 ? 65536 / (64 * ((1 << sigma) / E)) : 16);
 }
 
-template <class A, int SIGMA>
-__global__ void __launch_bounds__((1 << SIGMA) / 16, row_min_blocks(SIGMA)) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
+template <class A, int SIGMA, int E = 16>
+__global__ void __launch_bounds__((1 << SIGMA) / E, row_min_blocks(SIGMA, E)) k_row_fused(const LargeDesc d, ModParams m, TwTables tw) {
     pdl_launch_dependents();
-    row_body<A, SIGMA>(d, blockIdx.x, m, tw);
+    row_body<A, SIGMA, E>(d, blockIdx.x, m, tw);
+}
+
+// Words per thread of the row stage: 16 (one 512-word row per warp) when the
+// product has rows enough to fill the GPU, fewer -- more threads per row, a
+// shorter chain of dependent butterflies in each -- when its k rows x S/16
+// threads would leave most SMs with a warp or two (rows of up to 2^11 words).
+constexpr int ROW_E4_MAX_THREADS = 152 * 64;    // k S / 16 below this: E = 4
+constexpr int ROW_E8_MAX_THREADS = 152 * 256;   // below this: E = 8
+inline int row_words_per_thread(int sigma, int64_t k) {
+    if (sigma > 11) return 16;
+    const int64_t threads16 = k << (sigma - 4);
+    return threads16 < ROW_E4_MAX_THREADS ? 4 : (threads16 < ROW_E8_MAX_THREADS ? 8 : 16);
 }
 
 template <class A, int C, int TL>
@@ -175,13 +189,23 @@ static cudaError_t launch_col_t(const LargeDesc &d, ModParams m, TwTables tw, cu
 #undef PM_COL_CASE
 }
 
+template <class A, int SIGMA, int E>
+static cudaError_t launch_rows_e(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
+    constexpr int S = 1 << SIGMA;
+    const size_t smem = row_smem_bytes(SIGMA, E);
+    cudaError_t e = ensure_smem(k_row_fused<A, SIGMA, E>, smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_row_fused<A, SIGMA, E>, (int)d.g.k, S / E, smem, st, d, m, tw);
+}
+
 template <class A, int SIGMA>
 static cudaError_t launch_rows(const LargeDesc &d, ModParams m, TwTables tw, cudaStream_t st) {
-    constexpr int S = 1 << SIGMA;
-    const size_t smem = row_smem_bytes(SIGMA);
-    cudaError_t e = ensure_smem(k_row_fused<A, SIGMA>, smem);
-    if (e != cudaSuccess) return e;
-    return launch_pdl(k_row_fused<A, SIGMA>, (int)d.g.k, S / 16, smem, st, d, m, tw);
+    if constexpr (SIGMA <= 11) {
+        const int E = row_words_per_thread(SIGMA, d.g.k);
+        if (E == 4) return launch_rows_e<A, SIGMA, 4>(d, m, tw, st);
+        if (E == 8) return launch_rows_e<A, SIGMA, 8>(d, m, tw, st);
+    }
+    return launch_rows_e<A, SIGMA, 16>(d, m, tw, st);
 }
 
 template <class A>
