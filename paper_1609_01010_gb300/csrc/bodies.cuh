@@ -201,14 +201,15 @@ __device__ __forceinline__ void row_body(const LargeDesc &d, u32 ib, ModParams m
     stage_tw<SIGMA>(twb, tw.fwd, t, ib);
     if constexpr (EARLY) stage_tw<UL>(twlo, tw.inv, t, ib);
     cp_async_commit();
-    // The pointwise constant, fetched now so its latency is behind the passes.
-    const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
     pdl_wait();  // the rows come from the column-stage kernel
     u32 xa[E], xb[E];
     srow2_load_g<SIGMA, E>(xa, xb, rowa, d.wb + (int64_t)ib * S, tid);
     cp_async_wait<0>();
     __syncthreads();
     srow2_fwd_1b<A, SIGMA, 0, EARLY, E>(xa, xb, buf, twb, tid, p, tw.inv, t, ib);
+    // The pointwise constant, loaded here rather than before the passes: held
+    // through them it costs the 4096-word row two registers and a spill.
+    const uint2 cs = row_scale(tw, SIGMA, ib, (u32)d.g.k);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         PM_DCHECK(xa[i] < 2 * A::bound(p) && xb[i] < 2 * A::bound(p) && ib < (u32)d.g.k, tw.status);
