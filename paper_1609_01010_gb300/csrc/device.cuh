@@ -68,7 +68,7 @@ __device__ __forceinline__ void grp_fwd(u32 *x, const uint2 *__restrict__ tw, in
 
 // Same with per-level copy flags: bit d of copymask set means every upper
 // input at level lev0+d is zero, so the butterfly is (a, 0) -> (a, a).
-template <class A, int R>
+template <class A, int R, bool TS = false>
 __device__ __forceinline__ void grp_fwd_cp(u32 *x, const uint2 *__restrict__ tw, int lev0, u32 node0, u32 p,
                                            u32 copymask) {
 #pragma unroll
@@ -85,7 +85,8 @@ __device__ __forceinline__ void grp_fwd_cp(u32 *x, const uint2 *__restrict__ tw,
         } else {
 #pragma unroll
             for (int e = 0; e < (1 << d); ++e) {
-                const uint2 w = __ldg(tw + tw_index(lev0 + d, (node0 << d) + e));
+                const uint2 *q = tw + tw_index(lev0 + d, (node0 << d) + e);
+                const uint2 w = TS ? *q : __ldg(q);
 #pragma unroll
                 for (int jj = 0; jj < half; ++jj) {
                     const int lo = e * 2 * half + jj;
@@ -181,14 +182,15 @@ __device__ __forceinline__ void grp_inv2(u32 *x, u32 *y, const uint2 *itw, int l
     }
 }
 
-template <class A, int R>
+template <class A, int R, bool TS = false>
 __device__ __forceinline__ void grp_inv(u32 *x, const uint2 *__restrict__ itw, int lev0, u32 node0, u32 p) {
 #pragma unroll
     for (int d = R - 1; d >= 0; --d) {
         const int half = 1 << (R - 1 - d);
 #pragma unroll
         for (int e = 0; e < (1 << d); ++e) {
-            const uint2 w = __ldg(itw + tw_index(lev0 + d, (node0 << d) + e));
+            const uint2 *q = itw + tw_index(lev0 + d, (node0 << d) + e);
+            const uint2 w = TS ? *q : __ldg(q);
 #pragma unroll
             for (int jj = 0; jj < half; ++jj) {
                 const int lo = e * 2 * half + jj;
@@ -783,7 +785,7 @@ struct ColFwdArgs {
 };
 
 // One forward pass of R levels starting at depth s0.
-template <class A, int R, int C, int LAY, int SRC, int DST>
+template <class A, int R, int C, int LAY, int SRC, int DST, bool TS = false>
 __device__ __forceinline__ void colf_pass(const ColFwdArgs &X, int s0) {
     constexpr int logC = ilog2c(C);
     const int logM = X.t - s0, logJ = logM - R;
@@ -814,7 +816,7 @@ __device__ __forceinline__ void colf_pass(const ColFwdArgs &X, int s0) {
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q) x[q] = X.sm[ad.at(q)];
         }
-        grp_fwd_cp<A, R>(x, X.tw, s0, v, X.p, copymask);
+        grp_fwd_cp<A, R, TS>(x, X.tw, s0, v, X.p, copymask);
         if constexpr (DST == IO_GLOBAL) {
             const u32 e0 = (r0 << X.logS) + X.c0 + c;
             const int sh = logJ + X.logS;
@@ -833,14 +835,14 @@ __device__ __forceinline__ void colf_pass(const ColFwdArgs &X, int s0) {
     }
 }
 
-template <class A, int C, int LAY, int SRC, int DST>
+template <class A, int C, int LAY, int SRC, int DST, bool TS = false>
 __device__ __forceinline__ void colf_pass_r(int R, const ColFwdArgs &X, int s0) {
     // at most 4 levels: one 16-word register array; an if-chain over sizes
     // up to 4 keeps it in registers (a 32-word variant next to others spills it)
-    if (R == 4) colf_pass<A, 4, C, LAY, SRC, DST>(X, s0);
-    else if (R == 3) colf_pass<A, 3, C, LAY, SRC, DST>(X, s0);
-    else if (R == 2) colf_pass<A, 2, C, LAY, SRC, DST>(X, s0);
-    else colf_pass<A, 1, C, LAY, SRC, DST>(X, s0);
+    if (R == 4) colf_pass<A, 4, C, LAY, SRC, DST, TS>(X, s0);
+    else if (R == 3) colf_pass<A, 3, C, LAY, SRC, DST, TS>(X, s0);
+    else if (R == 2) colf_pass<A, 2, C, LAY, SRC, DST, TS>(X, s0);
+    else colf_pass<A, 1, C, LAY, SRC, DST, TS>(X, s0);
 }
 
 // Forward column stage of one tile.  The first pass reads the operand from
@@ -892,7 +894,7 @@ struct ColInvArgs {
 // Inverse pass of R levels [lev0, lev0+R) of the subtree rooted at (s_root,
 // i_root) covering rows [base, base + 2^logMroot); nodes at depth lev0 have
 // 2^logMsub rows.
-template <class A, int R, int C, int LAY, int SRC, int DST>
+template <class A, int R, int C, int LAY, int SRC, int DST, bool TS = false>
 __device__ __forceinline__ void coli_pass(const ColInvArgs &X, int lev0, int s_root, u32 i_root, int base,
                                           int logMsub, int logNodes) {
     constexpr int logC = ilog2c(C);
@@ -913,7 +915,7 @@ __device__ __forceinline__ void coli_pass(const ColInvArgs &X, int lev0, int s_r
 #pragma unroll
             for (int q = 0; q < (1 << R); ++q) x[q] = X.sm[ad.at(q)];
         }
-        grp_inv<A, R>(x, X.itw, lev0, (i_root << (lev0 - s_root)) + v, X.p);
+        grp_inv<A, R, TS>(x, X.itw, lev0, (i_root << (lev0 - s_root)) + v, X.p);
         if constexpr (DST == IO_GLOBAL) {
             const u32 e0 = (r0 << X.logS) + X.c0 + c;
             const int sh = logJ + X.logS;
@@ -931,20 +933,20 @@ __device__ __forceinline__ void coli_pass(const ColInvArgs &X, int lev0, int s_r
     }
 }
 
-template <class A, int C, int LAY, int SRC, int DST>
+template <class A, int C, int LAY, int SRC, int DST, bool TS = false>
 __device__ __forceinline__ void coli_pass_r(int R, const ColInvArgs &X, int lev0, int s_root, u32 i_root, int base,
                                             int logMsub, int logNodes) {
-    if (R == 4) coli_pass<A, 4, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
-    else if (R == 3) coli_pass<A, 3, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
-    else if (R == 2) coli_pass<A, 2, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
-    else coli_pass<A, 1, C, LAY, SRC, DST>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    if (R == 4) coli_pass<A, 4, C, LAY, SRC, DST, TS>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else if (R == 3) coli_pass<A, 3, C, LAY, SRC, DST, TS>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else if (R == 2) coli_pass<A, 2, C, LAY, SRC, DST, TS>(X, lev0, s_root, i_root, base, logMsub, logNodes);
+    else coli_pass<A, 1, C, LAY, SRC, DST, TS>(X, lev0, s_root, i_root, base, logMsub, logNodes);
 }
 
 // Unscaled inverse of the subtree (s, i) on rows [base, base + 2^lm): M times
 // its coefficients.  Passes run from the deepest levels up.  from_g: the
 // first pass reads the workspace; to_g: the last pass writes the product.
 // Ends with a barrier.
-template <class A, int C, int LAY>
+template <class A, int C, int LAY, bool TS = false>
 __device__ void coli_full(const ColInvArgs &X, int s, u32 i, int base, int lm, bool from_g, bool to_g) {
     if (lm == 0) return;
     const int np = col_npass(lm);
@@ -956,13 +958,13 @@ __device__ void coli_full(const ColInvArgs &X, int s, u32 i, int base, int lm, b
         const bool first = ch == np - 1, last = ch == 0;
         const int lev0 = s + d0, logMsub = lm - d0, logNodes = d0;
         if (first && from_g && last && to_g)
-            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_GLOBAL>(R, X, lev0, s, i, base, logMsub, logNodes);
+            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_GLOBAL, TS>(R, X, lev0, s, i, base, logMsub, logNodes);
         else if (first && from_g)
-            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_SMEM>(R, X, lev0, s, i, base, logMsub, logNodes);
+            coli_pass_r<A, C, LAY, IO_GLOBAL, IO_SMEM, TS>(R, X, lev0, s, i, base, logMsub, logNodes);
         else if (last && to_g)
-            coli_pass_r<A, C, LAY, IO_SMEM, IO_GLOBAL>(R, X, lev0, s, i, base, logMsub, logNodes);
+            coli_pass_r<A, C, LAY, IO_SMEM, IO_GLOBAL, TS>(R, X, lev0, s, i, base, logMsub, logNodes);
         else
-            coli_pass_r<A, C, LAY, IO_SMEM, IO_SMEM>(R, X, lev0, s, i, base, logMsub, logNodes);
+            coli_pass_r<A, C, LAY, IO_SMEM, IO_SMEM, TS>(R, X, lev0, s, i, base, logMsub, logNodes);
         __syncthreads();
     }
 }
@@ -1093,14 +1095,14 @@ __device__ __forceinline__ u32 half_mod(u32 x, u32 p) { return (x + (x & 1u) * p
 // read before written.  On exit rows [0, k) hold the coefficients.  Values
 // stay in [0, B) throughout.  Elementwise records handle two adjacent
 // columns per task.
-template <class A, int C, int LAY>
+template <class A, int C, int LAY, bool TS = false>
 __device__ void coli_steps(const ColInvArgs &X, const ItftStep *__restrict__ steps, int nsteps) {
     constexpr int logC2 = ilog2c(C) - 1;
     const u32 p = X.p, B = A::bound(p);
     for (int si = 0; si < nsteps; ++si) {
         const ItftStep st = steps[si];
         if (st.kind == ST_FULL) {
-            coli_full<A, C, LAY>(X, st.s, st.i, st.base, 31 - __clz(st.h), false, false);
+            coli_full<A, C, LAY, TS>(X, st.s, st.i, st.base, 31 - __clz(st.h), false, false);
             continue;
         }
         const bool upper = (st.kind == ST_PRE_RIGHT || st.kind == ST_PRE_LEFT);

@@ -7,8 +7,9 @@
 // decomposition going through distributed shared memory:
 //   1. CTA q copies columns [q*512/Q, (q+1)*512/Q) of all T rows of both
 //      operands into shared memory by cp.async, together with its rows'
-//      twiddles and the ITFT step list, and runs the column stage of the
-//      TFT on them (pruned to the input support and the k needed rows);
+//      twiddles, the column tree's twiddles and the ITFT step list, and runs
+//      the column stage of the TFT on them (pruned to the input support and
+//      the k needed rows);
 //   2. cluster barrier; CTA q gathers its T/Q rows (rows < k) from the Q
 //      column tiles, and all its threads (512/E per row, E = 4 or 8 words
 //      each) run the 9 row levels of both operands, the pointwise product
@@ -100,6 +101,13 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     }
     cp_async_commit();
     __shared__ __align__(16) ItftStep s_steps[SMALL_CL_MAX_STEPS];
+    // the column tree's forward and inverse twiddles (levels < t: table
+    // entries [0, T)), read by every task of the column passes
+    __shared__ uint2 s_ctw[2][G::T];
+    if (threadIdx.x < G::T) {
+        s_ctw[0][threadIdx.x] = __ldg(tw.fwd + threadIdx.x);
+        s_ctw[1][threadIdx.x] = __ldg(tw.inv + threadIdx.x);
+    }
     const bool steps_in_smem = d.nsteps <= SMALL_CL_MAX_STEPS;
     if (steps_in_smem) {
         constexpr int W4 = (int)(sizeof(ItftStep) / sizeof(uint4));
@@ -114,14 +122,14 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     {
         const int S = G::S;
         const int zba = (int)((d.za + S - 1) / S), zbb = (int)((d.zb + S - 1) / S);
-        ColFwdArgs X{tile_a, d.a, nullptr, d.za, c0, SMALL_LOG_S, G::T, LOGT, zba, k, d.prune != 0, tw.fwd, p,
+        ColFwdArgs X{tile_a, d.a, nullptr, d.za, c0, SMALL_LOG_S, G::T, LOGT, zba, k, d.prune != 0, s_ctw[0], p,
                      tw.status};
-        colf_pass_r<A, G::CP, LAY_SWZ, IO_SMEM, IO_SMEM>(LOGT, X, 0);
+        colf_pass_r<A, G::CP, LAY_SWZ, IO_SMEM, IO_SMEM, true>(LOGT, X, 0);
         X.sm = tile_b;
         X.g = d.b;
         X.z = d.zb;
         X.zb = zbb;
-        colf_pass_r<A, G::CP, LAY_SWZ, IO_SMEM, IO_SMEM>(LOGT, X, 0);
+        colf_pass_r<A, G::CP, LAY_SWZ, IO_SMEM, IO_SMEM, true>(LOGT, X, 0);
     }
     cl.sync();
 
@@ -180,8 +188,8 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     cl.sync();
 
     // 4. ITFT column stage and store
-    const ColInvArgs Y{tile_a, nullptr, d.c, d.n, c0, SMALL_LOG_S, k, tw.inv, p, tw.fwd, nullptr, tw.status};
-    coli_steps<A, G::CP, LAY_SWZ>(Y, steps_in_smem ? s_steps : d.steps, d.nsteps);
+    const ColInvArgs Y{tile_a, nullptr, d.c, d.n, c0, SMALL_LOG_S, k, s_ctw[1], p, s_ctw[0], nullptr, tw.status};
+    coli_steps<A, G::CP, LAY_SWZ, true>(Y, steps_in_smem ? s_steps : d.steps, d.nsteps);
     for (int e = threadIdx.x; e < k * G::CP; e += blockDim.x) {
         const int r = e / G::CP, lc = e % G::CP;
         const int64_t o = (int64_t)r * G::S + c0 + lc;
