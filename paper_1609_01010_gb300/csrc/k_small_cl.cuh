@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(SMALL_CL_THREADS) k_small_cl(SmallDesc d, ModP
     // the column tree's forward and inverse twiddles (levels < t: table
     // entries [0, T)), read by every task of the column passes
     __shared__ uint2 s_ctw[2][G::T];
-    if (threadIdx.x < G::T) {
-        s_ctw[0][threadIdx.x] = __ldg(tw.fwd + threadIdx.x);
-        s_ctw[1][threadIdx.x] = __ldg(tw.inv + threadIdx.x);
+    if (threadIdx.x < G::T) {  // entry 0 is not a tree node
+        s_ctw[0][threadIdx.x] = threadIdx.x ? __ldg(tw.fwd + threadIdx.x) : make_uint2(0u, 0u);
+        s_ctw[1][threadIdx.x] = threadIdx.x ? __ldg(tw.inv + threadIdx.x) : make_uint2(0u, 0u);
     }
     const bool steps_in_smem = d.nsteps <= SMALL_CL_MAX_STEPS;
     if (steps_in_smem) {
