@@ -187,6 +187,12 @@ cudaError_t launch_large(bool lazy, const LargeDesc &d, Schedule sch, ModParams 
                          cudaEvent_t *ev) {
     cudaError_t e;
     const bool tma = sch.C == TC && d.g.t >= 1 && d.g.t <= 10;
+    // The inverse column stage runs on the TMA-fed 32-column tiles also after
+    // an 8- or 128-column forward stage when the rows are long enough to give
+    // at least 128 tiles (S >= 4096): 36.96 against 37.38 us per product at
+    // L = 2^21; with 64 tiles (L = 2^20, S = 2048) it was slower, 25.9 against
+    // 23.9 us.
+    const bool tma_inv = d.g.t >= 1 && d.g.t <= 10 && (sch.C == TC || d.g.S >= 4096);
     ColMaps cm;
     if (ev) cudaEventRecord(ev[0], st);
     if (tma) {
@@ -201,7 +207,7 @@ cudaError_t launch_large(bool lazy, const LargeDesc &d, Schedule sch, ModParams 
     e = lazy ? launch_row_lazy(d, m, tw, st) : launch_row_strict(d, m, tw, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
-    if (tma) {
+    if (tma_inv) {
         memset(&cm, 0, sizeof cm);
         col_maps_inv(d, &cm);
         e = lazy ? launch_tcoli_lazy(d, m, tw, cm, st) : launch_tcoli_strict(d, m, tw, cm, st);
