@@ -75,3 +75,27 @@ def test_host_side_argument_checks(lib):
     assert L.polymul_strerror(-10).decode().startswith("an input coefficient")
     assert L.polymul_strerror(-6).decode().startswith("a bounded wait")
     assert b"sm_103a" in L.polymul_version()
+
+
+def test_schedule_and_batch_width_tables(lib):
+    """Host-side tables, no CUDA call: every built-in schedule (sigma, C) of
+    the three-kernel path is one the kernels take, and a batch's column-tile
+    width is the widest of 8 .. 2048 whose T x C words fit the 64 KB item
+    buffer (T = 2^(l - 12) rows of the batch's 4096-word rows)."""
+    from paper_1609_01010_gb300 import binding as B
+    L = B.lib()
+    sig, C = ctypes.c_int(), ctypes.c_int()
+    for l in range(10, 25):
+        assert L.polymul_get_schedule(l, ctypes.byref(sig), ctypes.byref(C)) == 0
+        t = l - sig.value
+        assert 9 <= sig.value <= 13 and C.value in (8, 32, 128) and 1 <= t <= 11, (l, sig.value, C.value)
+        # double-buffered tiles within 128 KB, except the TMA-fed 32-column tiles at t = 10
+        assert (2 << t) * C.value * 4 <= 128 * 1024 or (C.value == 32 and t == 10), l
+    assert L.polymul_get_schedule(9, ctypes.byref(sig), ctypes.byref(C)) == -7  # one-CTA sizes: no schedule
+    widths = (8, 32, 128, 256, 512, 1024, 2048)
+    for l in range(14, 23):
+        assert L.polymul_get_batch_width(l, ctypes.byref(C)) == 0
+        fits = [w for w in widths if (w << (l - 12)) * 4 <= 64 * 1024]
+        assert C.value == max(fits), (l, C.value)
+    assert L.polymul_get_batch_width(13, ctypes.byref(C)) == -7
+    assert L.polymul_get_batch_width(14, None) == -3
